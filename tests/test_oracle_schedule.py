@@ -1,0 +1,174 @@
+"""Pins of the oracle's schedule objects: closed-form wavefront numbers on grids and
+simple chains, order and partition invariants, validator verdicts on planted mistakes, and
+the reuse ratios of Table 2 (golden fixture). CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_12238_gb300 import inputs as I
+from tests._mats import dense_to_csr, random_lower, random_square
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_levels_grid2d_closed_form():
+    nx, ny = 7, 5
+    L = I.grid_lower_laplacian((nx, ny), 1)
+    M = I.grid_full_stencil_random((nx, ny), 1)
+    lev = oracle.levels(oracle.SEP, L, M)
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    x, y = x.ravel(), y.ravel()
+    assert np.array_equal(lev[: nx * ny], x + y)
+    # SpMV row (x,y) reads x at its forward neighbours (x+1,y), (x,y+1) when they exist
+    fwd = (x < nx - 1) | (y < ny - 1)
+    assert np.array_equal(lev[nx * ny:], np.where(fwd, x + y + 2, x + y + 1))
+    levT = oracle.levels(oracle.PAIRED_T, L)
+    assert np.array_equal(levT, (nx - 1 - x) + (ny - 1 - y))
+
+
+def test_levels_grid3d_closed_form():
+    d = (6, 4, 3)
+    L = I.grid_lower_laplacian(d, 2)
+    lev = oracle.levels(oracle.PAIRED, L)
+    z, y, x = np.indices(d[::-1]).reshape(3, -1)
+    assert np.array_equal(lev, x + y + z)
+    _, depth = oracle.order(lev, L.n_rows)
+    assert depth == sum(d) - 3 + 1
+
+
+def test_levels_chain_and_diagonal():
+    n = 9
+    bid = np.eye(n) * 2 + np.eye(n, k=-1)
+    assert np.array_equal(oracle.levels(oracle.PAIRED, dense_to_csr(bid)), np.arange(n))
+    assert np.array_equal(oracle.levels(oracle.PAIRED_T, dense_to_csr(bid)), n - 1 - np.arange(n))
+    dg = dense_to_csr(np.eye(n) * 3)
+    assert np.array_equal(oracle.levels(oracle.PAIRED, dg), np.zeros(n))
+    # SEP_T: A^T row j waits for every lambda_i with A_ij != 0; empty column -> level 0
+    A = np.zeros((n, n))
+    A[2, 5] = 1.0
+    A[7, 5] = 1.0
+    lev = oracle.levels(oracle.SEP_T, dense_to_csr(bid), dense_to_csr(A))
+    lam = n - 1 - np.arange(n)
+    want = np.zeros(n, dtype=np.int32)
+    want[5] = max(lam[2], lam[7]) + 1
+    assert np.array_equal(lev[n:], want)
+
+
+def _brute_levels(edges, nv):
+    """Longest path from sources by repeated relaxation (Bellman-Ford style), tiny inputs."""
+    lev = np.zeros(nv, dtype=np.int64)
+    for _ in range(nv + 1):
+        changed = False
+        for u, v in edges:
+            if lev[u] + 1 > lev[v]:
+                lev[v] = lev[u] + 1
+                changed = True
+        if not changed:
+            break
+    return lev
+
+
+@pytest.mark.parametrize("kind", [oracle.SEP, oracle.PAIRED, oracle.PAIRED_T, oracle.SEP_T])
+def test_levels_match_brute_force_relaxation(kind):
+    n = 30
+    DL = random_lower(n, 0.15, 61)
+    DM = random_square(n, 0.1, 62)
+    L, M = dense_to_csr(DL), dense_to_csr(DM)
+    edges = []
+    for i in range(n):
+        for j in range(i):
+            if DL[i, j] != 0:
+                edges.append((j, i) if kind in (oracle.SEP, oracle.PAIRED) else (i, j))
+    if kind == oracle.SEP:
+        edges += [(j, n + i) for i in range(n) for j in range(n) if DM[i, j] != 0]
+    if kind == oracle.SEP_T:
+        edges += [(i, n + j) for i in range(n) for j in range(n) if DM[i, j] != 0]
+    nv = oracle.n_vertices(kind, n)
+    assert np.array_equal(oracle.levels(kind, L, M if kind in (oracle.SEP, oracle.SEP_T) else None),
+                          _brute_levels(edges, nv))
+
+
+def test_order_sorted_by_level_tag_row_and_valid():
+    w = I.trsv_spmv_lap2d(12, seed=3)
+    lev = oracle.levels(oracle.SEP, w.L, w.M)
+    o, depth = oracle.order(lev, w.n)
+    tag = (o.view(np.uint32) >> 31).astype(np.int64)
+    row = (o.view(np.uint32) & 0x7FFFFFFF).astype(np.int64)
+    v = tag * w.n + row
+    assert np.array_equal(np.sort(v), np.arange(2 * w.n))
+    ref = np.lexsort((row, tag, lev[v]))
+    assert np.array_equal(ref, np.arange(2 * w.n))   # already in (level, tag, row) order
+    assert depth == lev.max() + 1
+    pp = oracle.partition(o, w.n, oracle.costs(oracle.COST_SEP, w.L, w.M), 40)
+    assert oracle.validate(oracle.SEP, w.L, w.M, o, pp) == 0
+
+
+@pytest.mark.parametrize("target", [1, 7, 64, 10 ** 9])
+def test_partition_cut_invariants(target):
+    w = I.trsv_spmv_lap2d(9, seed=4)
+    s = oracle.schedule(oracle.SEP, oracle.COST_SEP, w.L, w.M, target)
+    o, pp, c = s["order"], s["part_ptr"], s["cost"]
+    v = (o.view(np.uint32) >> 31).astype(np.int64) * w.n + (o.view(np.uint32) & 0x7FFFFFFF)
+    S = np.concatenate([[0], np.cumsum(c[v])])[:-1]
+    q = S // target
+    assert pp[0] == 0 and pp[-1] == len(o) and np.all(np.diff(pp) > 0)
+    for p in range(len(pp) - 1):
+        seg = q[pp[p]:pp[p + 1]]
+        assert np.all(seg == seg[0])                 # one quotient per partition
+        if p + 1 < len(pp) - 1:
+            assert q[pp[p + 1]] > seg[0]             # maximal runs
+    if target == 1:
+        assert len(pp) - 1 == len(o)
+    if target == 10 ** 9:
+        assert len(pp) - 1 == 1
+
+
+def test_costs_hand_computed():
+    # L = [[1,0,0],[1,1,0],[1,1,1]], M = [[1,0,1],[0,1,0],[0,0,1]]
+    L = dense_to_csr(np.tril(np.ones((3, 3))))
+    M = dense_to_csr(np.array([[1.0, 0, 1], [0, 1, 0], [0, 0, 1]]))
+    assert oracle.costs(oracle.COST_SEP, L, M).tolist() == [2, 3, 4, 3, 2, 2]
+    assert oracle.costs(oracle.COST_TRSV, L).tolist() == [2, 3, 4]
+    # IC0 row i touches its row and each earlier row j of the pattern: 1+0, 2+1, 3+(1+2)
+    assert oracle.costs(oracle.COST_IC0, L).tolist() == [2, 4, 7]
+    assert oracle.costs(oracle.COST_IC0_TRSV, L).tolist() == [3, 6, 10]
+    assert oracle.costs(oracle.COST_SPMV_TRSV, L, M).tolist() == [4, 4, 5]
+    # column counts: L^T rows 3,2,1; M^T rows 1,1,2
+    assert oracle.costs(oracle.COST_PAIRED_T, L, M).tolist() == [1 + 3 + 1 + 2 + 1, 1 + 2 + 2 + 1 + 1,
+                                                                 2 + 1 + 3 + 1 + 1]
+    assert oracle.costs(oracle.COST_SEP_T, L, M).tolist() == [3 + 1 + 2 + 1, 2 + 2 + 1 + 1, 1 + 3 + 1 + 1,
+                                                              2, 2, 3]
+
+
+def test_validator_catches_planted_mistakes():
+    w = I.trsv_spmv_lap2d(8, seed=5)
+    s = oracle.schedule(oracle.SEP, oracle.COST_SEP, w.L, w.M, 30)
+    o, pp = s["order"].copy(), s["part_ptr"]
+    assert oracle.validate(oracle.SEP, w.L, w.M, o, pp) == 0
+    bad = o.copy()
+    bad[[0, -1]] = bad[[-1, 0]]                       # a sink before a source
+    assert oracle.validate(oracle.SEP, w.L, w.M, bad, pp) == 2
+    dup = o.copy()
+    dup[3] = dup[4]
+    assert oracle.validate(oracle.SEP, w.L, w.M, dup, pp) == 1
+    badp = pp.copy()
+    badp[1] = badp[2]
+    assert oracle.validate(oracle.SEP, w.L, w.M, o, badp) == 3
+    # the transposed schedule must be reversed: the forward order is invalid for PAIRED_T
+    sT = oracle.schedule(oracle.PAIRED_T, oracle.COST_PAIRED_T, w.L, w.M, 30)
+    assert oracle.validate(oracle.PAIRED_T, w.L, None, sT["order"], sT["part_ptr"]) == 0
+    sF = oracle.schedule(oracle.PAIRED, oracle.COST_TRSV, w.L, None, 30)
+    assert oracle.validate(oracle.PAIRED_T, w.L, None, sF["order"], sF["part_ptr"]) == 2
+
+
+def test_reuse_ratio_table2_golden():
+    with open(os.path.join(GOLDEN, "reuse_ratio_table2.json")) as f:
+        g = json.load(f)
+    for case in g["cases"]:
+        num, den = case["expected"].split("/")
+        got = oracle.reuse_ratio(case["pair"], case["n"], case["size_L"], case["size_M"])
+        assert got == pytest.approx(float(num) / float(den), rel=1e-15)
+        assert (got >= 1.0) == case["interleaved"]

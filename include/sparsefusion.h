@@ -1,0 +1,214 @@
+/*
+ * sparsefusion.h - C ABI of the GB300 (sm_103a) sparse-fusion library.
+ *
+ * Sparse fusion (Cheshmi, Strout, Mehri Dehnavi, "Composing Loop-carried Dependence with
+ * Other Loops", arXiv 2111.12238) runs two sparse kernels, at least one of which has
+ * loop-carried dependences, as one parallel pass. An inspector (§2.2) builds a fused
+ * schedule from the two kernels' dependence DAGs and the inter-kernel dependence matrix F;
+ * an executor (§2.3, Figure 4) runs the fused schedule. This header exposes that
+ * inspector-executor split (the driver of Figure 3b: intra_DAG, inter_DAG, compute_reuse,
+ * scheduling, then fused_code) as plain C calls.
+ *
+ * Conventions for every call:
+ *  - Array arguments are DEVICE pointers owned by the caller unless stated otherwise;
+ *    they must stay valid until the stream work that uses them has finished.
+ *  - CSR patterns: int32 rowptr[n_rows+1] with rowptr[0] = 0 and rowptr[n_rows] = nnz,
+ *    int32 colidx[nnz] strictly ascending within each row. Lower-triangular operands
+ *    (SpTRSV / SpIC0 patterns) hold only columns <= row and every row holds its diagonal
+ *    as its LAST entry. nnz < 2^31.
+ *  - Value arrays follow their pattern's CSR order. Dense blocks (right-hand sides,
+ *    solutions) are n x k ROW-MAJOR (the k values of one row are contiguous).
+ *  - Element type is chosen per call by sf_dtype: SF_F64 = double, SF_F32 = float.
+ *  - Calls that launch device work are stream-ordered and asynchronous; `stream` is a
+ *    cudaStream_t (NULL = legacy default stream). Device-side failures (a timed-out
+ *    dependence wait, an incomplete-Cholesky breakdown, a non-finite pivot) are recorded
+ *    in the schedule and reported by sf_schedule_check.
+ *  - Errors never trap or abort: every call returns an sf_status; sf_last_error_detail
+ *    gives a human-readable reason for the last failure on the calling thread.
+ */
+#ifndef SPARSEFUSION_H
+#define SPARSEFUSION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SF_OK = 0,
+    SF_ERR_INVALID_ARG = 1,  /* a NULL pointer, size or option out of range          */
+    SF_ERR_BAD_PATTERN = 2,  /* CSR pattern violates the conventions above           */
+    SF_ERR_CUDA = 3,         /* a CUDA runtime call failed                            */
+    SF_ERR_OOM = 4,          /* device allocation failed                              */
+    SF_ERR_TIMEOUT = 5,      /* a dependence wait in a kernel exceeded its time limit */
+    SF_ERR_BREAKDOWN = 6,    /* zero fill-in IC hit a non-positive pivot               */
+    SF_ERR_NONFINITE = 7,    /* a diagonal entry used as divisor was zero             */
+    SF_ERR_UNSUPPORTED = 8   /* the combination of pair / dtype / k is not provided   */
+} sf_status;
+
+/* The fused kernel pairs (Table 2 of the paper, restated in CSR form):
+ *  SF_TRSV_SPMV  combination 4: x = L^-1 b (SpTRSV), then y = M x (SpMV). F = pattern(M).
+ *  SF_IC0_TRSV   combination 5: L L^T ~ A by zero fill-in IC (SpIC0), then y = L^-1 b.
+ *                F = I: row i of the solve waits for row i of the factor.
+ *  SF_SPMV_TRSV  combination 2: r = b - A x_in (SpMV), then z = L^-1 r with L = tril(A)
+ *                passed as its own CSR (one Gauss-Seidel half-sweep). F = I.
+ * Single-kernel schedules, the building blocks of the unfused two-launch path:
+ *  SF_TRSV       x = L^-1 b alone.
+ *  SF_IC0        the zero fill-in IC factor alone.                                      */
+typedef enum { SF_TRSV_SPMV = 0, SF_IC0_TRSV = 1, SF_SPMV_TRSV = 2, SF_TRSV = 3, SF_IC0 = 4 } sf_pair;
+
+typedef enum { SF_F64 = 0, SF_F32 = 1 } sf_dtype;
+
+/* A CSR pattern (no values). rowptr / colidx are device pointers owned by the caller;
+ * sf_inspect copies what it needs, so they may be freed once sf_inspect returns. */
+typedef struct {
+    int32_t n_rows;
+    int32_t n_cols;
+    int64_t nnz;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+} sf_csr;
+
+/* Options; a zero-initialised struct selects every default. */
+#define SF_WANT_ADJOINT 0x1u /* also build the transposed schedule used by sf_adjoint */
+typedef struct {
+    int64_t part_cost_target; /* C of the partition cut (§3.1 vertex cost); 0 = auto  */
+    int32_t lanes_per_row;    /* lanes of a warp working on one row: 1..32 (pow2); 0 = auto */
+    int32_t rhs_tile;         /* right-hand-side columns handled side by side; 0 = auto */
+    int32_t g2_placement;     /* reserved, must be 0 (as-soon-as-possible placement) */
+    int32_t reserved;         /* must be 0 */
+    uint64_t timeout_ns;      /* limit of one dependence wait on the GPU; 0 = 2 s    */
+    uint32_t flags;           /* SF_WANT_ADJOINT                                      */
+    uint32_t reserved2;       /* must be 0 */
+} sf_options;
+
+/* Opaque fused schedule (§3.1 "fused partitioning", the FusedSchedule of Figure 3b).
+ * Owned by the library; device memory it holds is released by sf_schedule_destroy. */
+typedef struct sf_schedule sf_schedule;
+
+/* Inspector (§2.2, §3): build the fused schedule of `pair` on the GPU.
+ *  L: the lower-triangular pattern (SpTRSV's matrix; tril(A) for SF_IC0_TRSV, SF_IC0 and
+ *     SF_SPMV_TRSV). Square.
+ *  M: SF_TRSV_SPMV: the SpMV operand (n x n); SF_SPMV_TRSV: A (n x n); otherwise NULL.
+ * Builds the joint DAG (the SpTRSV DAG is the pattern of L, §2.2; F as listed for
+ * sf_pair), its wavefront levels by parallel Kahn peeling, the linear order by
+ * (level, kernel, row), and contiguous partitions of that order cut by vertex cost
+ * (§3.1). Synchronises `stream` before returning. On success *out owns a new schedule;
+ * on failure *out is NULL. */
+sf_status sf_inspect(sf_pair pair, const sf_csr *L, const sf_csr *M, const sf_options *opt,
+                     void *stream, sf_schedule **out);
+
+/* Batched inspector: `count` independent instances (host arrays Ls[count], Ms[count] of
+ * patterns with device pointers; Ms may be NULL when the pair has no M) scheduled as one
+ * block-diagonal system in a single queue ordered by (level, instance, row). Value
+ * arrays and dense blocks passed to sf_execute / sf_adjoint for a batched schedule are
+ * the instances' arrays concatenated in instance order. */
+sf_status sf_inspect_batched(sf_pair pair, int32_t count, const sf_csr *Ls, const sf_csr *Ms,
+                             const sf_options *opt, void *stream, sf_schedule **out);
+
+/* Executor (§2.3): one persistent launch that runs the fused schedule.
+ *  L_vals: SF_TRSV_SPMV, SF_SPMV_TRSV, SF_TRSV: values of L; SF_IC0_TRSV, SF_IC0: the
+ *          values of tril(A) to factor (input, not modified).
+ *  M_vals: SF_TRSV_SPMV: values of M; SF_SPMV_TRSV: values of A; otherwise NULL.
+ *  x_in:   SF_SPMV_TRSV only: the SpMV operand (n x k); otherwise NULL.
+ *  b:      right-hand side (n x k); NULL for SF_IC0.
+ *  y:      result (n x k): y = M L^-1 b, y = L^-1 b (IC0 factor L), z = L^-1 (b - A x_in),
+ *          or x = L^-1 b for SF_TRSV; NULL for SF_IC0.
+ *  x_save: optional. SF_TRSV_SPMV: receives the intermediate x = L^-1 b (n x k), needed by
+ *          sf_adjoint. SF_IC0_TRSV / SF_IC0: receives the factor values on L's pattern
+ *          (required for SF_IC0). When NULL a library-owned buffer is used; it is
+ *          allocated on the first call that needs it, so make one such call before
+ *          capturing the stream into a CUDA graph.
+ *  k:      number of right-hand sides, 1 <= k <= 1024.
+ * Concurrent calls with the same schedule on different streams race; calls on one
+ * stream are ordered. Returns after enqueueing the launch. */
+sf_status sf_execute(const sf_schedule *sch, sf_dtype dt, int32_t k, const void *L_vals,
+                     const void *M_vals, const void *x_in, const void *b, void *y, void *x_save,
+                     void *stream);
+
+/* Adjoint executor (not in the paper): gradients of the fused pair as one fused pass over
+ * the transposed schedule (requires SF_WANT_ADJOINT at inspection).
+ *  SF_TRSV_SPMV (y = M L^-1 b, x = L^-1 b): saved = x, gy = dL/dy. Computes u = M^T gy
+ *    and lam = L^-T u; writes gb = lam, and when non-NULL gL_vals (pattern of L) with
+ *    gL_ij = -sum_c lam_ic x_jc and gM_vals (pattern of M) with gM_ij = sum_c gy_ic x_jc.
+ *    gx_in must be NULL.
+ *  SF_SPMV_TRSV (z = L^-1 (b - A x_in)): saved = z, gy = dL/dz. Computes lam = L^-T gz;
+ *    writes gb = lam, and when non-NULL gx_in = -A^T lam, gL_vals with gL_ij =
+ *    -sum_c lam_ic z_jc, gM_vals (pattern of A) with gA_ij = -sum_c lam_ic x_in_jc.
+ * Other pairs return SF_ERR_UNSUPPORTED. Same stream and ownership rules as sf_execute. */
+sf_status sf_adjoint(const sf_schedule *sch, sf_dtype dt, int32_t k, const void *L_vals,
+                     const void *M_vals, const void *x_in, const void *saved, const void *gy,
+                     void *gb, void *gx_in, void *gL_vals, void *gM_vals, void *stream);
+
+/* Plain SpMV building block of the unfused path: y = M x (b == NULL) or y = b - M x.
+ * M is n_rows x n_cols; x is n_cols x k, b and y are n_rows x k. Asynchronous. */
+sf_status sf_spmv(sf_dtype dt, int32_t k, const sf_csr *M, const void *M_vals, const void *x,
+                  const void *b, void *y, void *stream);
+
+/* Synchronises `stream`, then reports (and clears) the first device-side failure recorded
+ * by executions of this schedule: SF_ERR_TIMEOUT, SF_ERR_BREAKDOWN or SF_ERR_NONFINITE;
+ * *row (may be NULL) receives the row involved, or -1. */
+sf_status sf_schedule_check(const sf_schedule *sch, void *stream, int32_t *row);
+
+/* Host-side validity check of the schedule (§3.2: every intra- and inter-kernel
+ * dependence must be honoured): copies the order, partitions and patterns to the host
+ * and checks that the order is a permutation of the joint DAG's vertices, that every DAG
+ * and F edge points forward in it, and that the partitions are contiguous and cover it.
+ * Checks the adjoint schedule too when present. Synchronous. SF_OK when valid,
+ * SF_ERR_BAD_PATTERN otherwise. */
+sf_status sf_validate(const sf_schedule *sch);
+
+/* Depth (number of wavefronts of the joint DAG), number of partitions and number of
+ * joint-DAG vertices of the forward schedule. Host memory outputs; any may be NULL. */
+sf_status sf_schedule_info(const sf_schedule *sch, int32_t *depth, int32_t *n_parts,
+                           int64_t *n_items);
+
+/* Extended description of a schedule. */
+typedef struct {
+    int32_t pair, n, k_hint, instances;
+    int32_t depth, n_parts;            /* forward schedule */
+    int64_t n_items;
+    int32_t adj_depth, adj_n_parts;    /* adjoint schedule, 0 when absent */
+    int64_t adj_n_items;
+    int32_t lanes_per_row, rhs_tile;
+    int64_t part_cost_target, adj_part_cost_target;
+    int32_t packing;                   /* 0 separated, 1 interleaved (paired rows) */
+    int32_t reserved;
+    double reuse_ratio;                /* Table 2 / §2.2 reuse ratio of the pair */
+    double inspect_ms;                 /* wall time of the inspector call */
+} sf_info;
+sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
+
+/* Copies one schedule to HOST buffers for inspection and tests. which = 0 forward,
+ * 1 adjoint. level[n_items] (wavefront of each vertex, vertex v = kernel*n + row),
+ * order[n_items] (row | kernel << 31 in execution order), part_ptr[n_parts+1];
+ * any pointer may be NULL. Synchronous. */
+sf_status sf_schedule_export(const sf_schedule *sch, int32_t which, int32_t *level,
+                             int32_t *order, int32_t *part_ptr);
+
+/* Changes launch parameters without re-inspecting: lanes_per_row (1..32, pow2) and
+ * rhs_tile (1..lanes_per_row, pow2); 0 keeps the current value. */
+sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_t rhs_tile);
+
+/* Sets the time limit of one dependence wait (0 = 2 s). */
+sf_status sf_schedule_set_timeout(sf_schedule *sch, uint64_t timeout_ns);
+
+/* Testing hook: swaps two entries of the forward order (positions q1 and q2) on the
+ * device, producing a schedule that may violate a dependence. An execution of such a
+ * schedule ends through the bounded dependence wait with SF_ERR_TIMEOUT reported by
+ * sf_schedule_check, never by a hang. */
+sf_status sf_schedule_debug_swap(sf_schedule *sch, int64_t q1, int64_t q2);
+
+void sf_schedule_destroy(sf_schedule *sch);
+
+const char *sf_status_string(sf_status s);
+
+/* Copies the thread-local description of the last failure into buf (NUL-terminated). */
+sf_status sf_last_error_detail(char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPARSEFUSION_H */

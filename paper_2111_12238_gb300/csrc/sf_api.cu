@@ -1,0 +1,729 @@
+// C ABI of libsparsefusion.so: argument validation, the schedule object, the inspector
+// driver (the runtime half of the paper's Figure 3b driver: DAGs, F, reuse ratio,
+// scheduling) and executor launches. No call here traps or throws across the ABI.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sf_inspect.cuh"
+
+#define SF_API extern "C" __attribute__((visibility("default")))
+
+using namespace sf;
+
+namespace {
+
+thread_local char g_detail[512] = "";
+
+sf_status fail(sf_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_detail, sizeof g_detail, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sf_status from_cuda(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(SF_ERR_OOM, "%s: out of device memory", what);
+    return fail(SF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SF_CK(call, what)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return from_cuda(e_, what); \
+    } while (0)
+
+const char *pat_name(unsigned code) {
+    switch (code) {
+        case PAT_ROWPTR0: return "rowptr[0] != 0";
+        case PAT_NNZ: return "rowptr[n_rows] != nnz";
+        case PAT_ROWPTR: return "rowptr not monotone or out of range";
+        case PAT_COL_RANGE: return "column index out of range";
+        case PAT_UNSORTED: return "columns not strictly ascending";
+        case PAT_DIAG: return "diagonal missing or not the last entry of the row";
+        default: return "invalid pattern";
+    }
+}
+
+struct Dir {
+    bool present = false;
+    int kind = 0;
+    long long nv = 0;
+    int depth = 0;
+    int n_parts = 0;
+    long long C = 0;
+    int *level = nullptr;
+    int *order = nullptr;
+    int *part_ptr = nullptr;
+    unsigned *flags = nullptr;
+    ExecState *st = nullptr;
+};
+
+const ExecState kInitState = {0u, 0u, 1u, 0u, 0u, 0, 0u, 0u};
+
+int pow2_ceil(long long v) {
+    int p = 1;
+    while (p < v && p < (1 << 30)) p <<= 1;
+    return p;
+}
+bool is_pow2_upto32(int v) { return v >= 1 && v <= 32 && (v & (v - 1)) == 0; }
+
+double reuse_ratio(sf_pair pair, long long n, long long sl, long long sm) {
+    // Table 2 / §2.2: common accesses over the larger kernel's accesses
+    switch (pair) {
+        case SF_TRSV_SPMV: return (double)(2 * n) / (double)std::max(sl + 2 * n, sm + 2 * n);
+        case SF_IC0_TRSV: return (double)(2 * sl) / (double)std::max(sl, sl + 2 * n);
+        case SF_SPMV_TRSV: return (double)(2 * n) / (double)std::max(sm + 2 * n, sl + 2 * n);
+        default: return 0.0;
+    }
+}
+
+}  // namespace
+
+struct sf_schedule {
+    sf_pair pair = SF_TRSV;
+    int n = 0;
+    int instances = 1;
+    Arena keep;
+    DevCsr L, M;
+    bool hasM = false;
+    DevCsrT LT, MT;
+    bool hasLT = false, hasMT = false;
+    Dir fwd, adj;
+    int lpr = 4, kt = 0;
+    unsigned long long timeout_ns = 2000000000ull;
+    double reuse = 0.0, inspect_ms = 0.0;
+    int packing = 0;
+    std::mutex mu;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int device = 0;
+    int sms = 1;
+};
+
+namespace {
+
+sf_status validate_options(const sf_options *o) {
+    if (!o) return SF_OK;
+    if (o->part_cost_target < 0) return fail(SF_ERR_INVALID_ARG, "part_cost_target must be >= 0");
+    if (o->lanes_per_row != 0 && !is_pow2_upto32(o->lanes_per_row))
+        return fail(SF_ERR_INVALID_ARG, "lanes_per_row must be 0 or a power of two in [1, 32]");
+    if (o->rhs_tile != 0 && !is_pow2_upto32(o->rhs_tile))
+        return fail(SF_ERR_INVALID_ARG, "rhs_tile must be 0 or a power of two in [1, 32]");
+    if (o->g2_placement != 0 || o->reserved != 0 || o->reserved2 != 0)
+        return fail(SF_ERR_INVALID_ARG, "g2_placement and reserved fields must be 0");
+    if (o->flags & ~SF_WANT_ADJOINT) return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
+    return SF_OK;
+}
+
+bool pair_has_M(sf_pair p) { return p == SF_TRSV_SPMV || p == SF_SPMV_TRSV; }
+bool pair_valid(sf_pair p) { return p >= SF_TRSV_SPMV && p <= SF_IC0; }
+
+sf_status check_csr_args(const sf_csr *m, const char *name, bool square) {
+    if (!m) return fail(SF_ERR_INVALID_ARG, "%s is NULL", name);
+    if (m->n_rows < 1 || m->n_cols < 1) return fail(SF_ERR_INVALID_ARG, "%s: empty matrix", name);
+    if (square && m->n_rows != m->n_cols) return fail(SF_ERR_INVALID_ARG, "%s must be square", name);
+    if (m->nnz < 0 || m->nnz >= (1LL << 31)) return fail(SF_ERR_INVALID_ARG, "%s: nnz out of range", name);
+    if (!m->rowptr || (m->nnz > 0 && !m->colidx)) return fail(SF_ERR_INVALID_ARG, "%s: NULL pattern array", name);
+    return SF_OK;
+}
+
+sf_status copy_pattern(sf_schedule *S, const sf_csr *src, DevCsr &dst, cudaStream_t s) {
+    dst.n_rows = src->n_rows;
+    dst.n_cols = src->n_cols;
+    dst.nnz = src->nnz;
+    dst.rowptr = (int *)S->keep.alloc(sizeof(int) * ((size_t)src->n_rows + 1));
+    dst.colidx = (int *)S->keep.alloc(sizeof(int) * (size_t)std::max<long long>(src->nnz, 1));
+    if (!dst.rowptr || !dst.colidx) return fail(SF_ERR_OOM, "pattern copy: out of device memory");
+    SF_CK(cudaMemcpyAsync(dst.rowptr, src->rowptr, sizeof(int) * ((size_t)src->n_rows + 1), cudaMemcpyDeviceToDevice, s),
+          "pattern copy");
+    if (src->nnz > 0)
+        SF_CK(cudaMemcpyAsync(dst.colidx, src->colidx, sizeof(int) * (size_t)src->nnz, cudaMemcpyDeviceToDevice, s),
+              "pattern copy");
+    return SF_OK;
+}
+
+sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user, cudaStream_t s, Arena &tmp) {
+    const int n = S->n;
+    d.kind = kind;
+    d.nv = (kind == K_SEP || kind == K_SEP_T) ? 2LL * n : (long long)n;
+    const long long nv = d.nv;
+    d.level = (int *)S->keep.alloc(sizeof(int) * nv);
+    d.order = (int *)S->keep.alloc(sizeof(int) * nv);
+    d.part_ptr = (int *)S->keep.alloc(sizeof(int) * (nv + 1));
+    d.flags = (unsigned *)S->keep.alloc(sizeof(unsigned) * (size_t)n);
+    d.st = (ExecState *)S->keep.alloc(sizeof(ExecState));
+    int *cost = (int *)tmp.alloc(sizeof(int) * nv);
+    long long *Sx = (long long *)tmp.alloc(sizeof(long long) * (nv + 1));
+    if (!d.level || !d.order || !d.part_ptr || !d.flags || !d.st || !cost || !Sx)
+        return fail(SF_ERR_OOM, "inspector: out of device memory");
+    SF_CK(cudaMemsetAsync(d.flags, 0, sizeof(unsigned) * (size_t)n, s), "inspector");
+    SF_CK(cudaMemcpyAsync(d.st, &kInitState, sizeof(ExecState), cudaMemcpyHostToDevice, s), "inspector");
+    // successor lists of the joint DAG (§2.2): forward DAG edges j -> i come from the
+    // transposed L (column j of L), F edges from the transposed M; the reversed DAGs of
+    // the adjoint use the rows of L (and of A) directly
+    const int *s1rp, *s1ci, *s2rp = nullptr, *s2ci = nullptr;
+    if (kind == K_SEP || kind == K_PAIRED) {
+        s1rp = S->LT.t.rowptr;
+        s1ci = S->LT.t.colidx;
+        if (kind == K_SEP) {
+            s2rp = S->MT.t.rowptr;
+            s2ci = S->MT.t.colidx;
+        }
+    } else {
+        s1rp = S->L.rowptr;
+        s1ci = S->L.colidx;
+        if (kind == K_SEP_T) {
+            s2rp = S->M.rowptr;
+            s2ci = S->M.colidx;
+        }
+    }
+    bool timed_out = false;
+    cudaError_t e = kahn_levels(nv, n, s1rp, s1ci, s2rp, s2ci, d.level, &d.depth, s, tmp, &timed_out);
+    if (e == cudaErrorInvalidValue) return fail(SF_ERR_BAD_PATTERN, "inspector: the joint DAG has a cycle");
+    if (e != cudaSuccess) return from_cuda(e, "Kahn peeling");
+    if (timed_out) return fail(SF_ERR_TIMEOUT, "Kahn peeling: grid barrier timed out");
+    e = build_order(nv, n, d.level, d.depth, d.order, s, tmp);
+    if (e != cudaSuccess) return from_cuda(e, "ordering");
+    e = vertex_costs(what, n, S->L, S->hasM ? &S->M : nullptr, S->hasLT ? &S->LT : nullptr,
+                     S->hasMT ? &S->MT : nullptr, cost, s);
+    if (e != cudaSuccess) return from_cuda(e, "vertex costs");
+    long long total = 0;
+    e = prefix_costs(nv, n, d.order, cost, Sx, &total, s, tmp);
+    if (e != cudaSuccess) return from_cuda(e, "cost prefix");
+    long long C = C_user;
+    if (C <= 0) {
+        const long long mean = std::max<long long>(1, (total + nv - 1) / nv);
+        C = (long long)(32 / S->lpr) * 2 * mean;
+    }
+    d.C = C;
+    e = cut_partitions(nv, Sx, C, d.part_ptr, &d.n_parts, s, tmp);
+    if (e != cudaSuccess) return from_cuda(e, "partition cut");
+    d.present = true;
+    return SF_OK;
+}
+
+sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
+    Arena tmp;
+    unsigned long long pst = 0;
+    SF_CK(check_pattern(S->L, 1, &pst, s, tmp), "pattern check");
+    if (pst != ~0ull)
+        return fail(SF_ERR_BAD_PATTERN, "L: %s (row %d)", pat_name((unsigned)(pst >> 32)), (int)(pst & 0xffffffffu));
+    if (S->hasM) {
+        SF_CK(check_pattern(S->M, 0, &pst, s, tmp), "pattern check");
+        if (pst != ~0ull)
+            return fail(SF_ERR_BAD_PATTERN, "M: %s (row %d)", pat_name((unsigned)(pst >> 32)), (int)(pst & 0xffffffffu));
+    }
+    const bool want_adj = (o.flags & SF_WANT_ADJOINT) != 0;
+    SF_CK(transpose_csr(S->L, S->LT, s, tmp, S->keep), "transpose of L");
+    S->hasLT = true;
+    if (S->pair == SF_TRSV_SPMV || (S->pair == SF_SPMV_TRSV && want_adj)) {
+        SF_CK(transpose_csr(S->M, S->MT, s, tmp, S->keep), "transpose of M");
+        S->hasMT = true;
+    }
+    // launch shape: lanes per row from the mean number of nonzeros per joint-DAG vertex
+    if (o.lanes_per_row) {
+        S->lpr = o.lanes_per_row;
+    } else {
+        const long long nnz = S->L.nnz + (S->hasM ? S->M.nnz : 0);
+        const long long nv = (S->pair == SF_TRSV_SPMV) ? 2LL * S->n : S->n;
+        const long long mean = std::max<long long>(1, (nnz + nv - 1) / nv);
+        S->lpr = std::min(32, pow2_ceil((mean + 1) / 2));
+    }
+    S->kt = o.rhs_tile;
+    if (S->kt > S->lpr) S->lpr = S->kt;
+    int kind = K_PAIRED, what = 5;
+    switch (S->pair) {
+        case SF_TRSV_SPMV: kind = K_SEP; what = 0; break;
+        case SF_IC0_TRSV: kind = K_PAIRED; what = 4; break;
+        case SF_SPMV_TRSV: kind = K_PAIRED; what = 3; break;
+        case SF_TRSV: kind = K_PAIRED; what = 5; break;
+        case SF_IC0: kind = K_PAIRED; what = 6; break;
+    }
+    S->packing = (kind == K_SEP) ? 0 : 1;
+    sf_status st = build_dir(S, S->fwd, kind, what, o.part_cost_target, s, tmp);
+    if (st != SF_OK) return st;
+    if (want_adj) {
+        if (S->pair == SF_TRSV_SPMV) st = build_dir(S, S->adj, K_PAIRED_T, 1, o.part_cost_target, s, tmp);
+        else st = build_dir(S, S->adj, K_SEP_T, 2, o.part_cost_target, s, tmp);
+        if (st != SF_OK) return st;
+    }
+    S->reuse = reuse_ratio(S->pair, S->n, S->L.nnz, S->hasM ? S->M.nnz : 0);
+    SF_CK(cudaStreamSynchronize(s), "inspector");
+    return SF_OK;
+}
+
+sf_status finish_inspect(sf_schedule *S, const sf_options &o, cudaStream_t s, sf_schedule **out,
+                         std::chrono::steady_clock::time_point t0) {
+    sf_status st = build_schedule(S, o, s);
+    if (st != SF_OK) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        delete S;
+        return st;
+    }
+    if (o.timeout_ns) S->timeout_ns = o.timeout_ns;
+    S->inspect_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = S;
+    return SF_OK;
+}
+
+sf_schedule *new_schedule(sf_pair pair) {
+    sf_schedule *S = new (std::nothrow) sf_schedule();
+    if (!S) return nullptr;
+    S->pair = pair;
+    cudaGetDevice(&S->device);
+    cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
+    if (S->sms < 1) S->sms = 1;
+    return S;
+}
+
+sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void **out) {
+    sf_schedule *S = const_cast<sf_schedule *>(Sc);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->scratch_bytes >= bytes) {
+        *out = S->scratch;
+        return SF_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(SF_ERR_INVALID_ARG, "this call needs a library-owned buffer that is allocated on first use; "
+                                        "make one such call before capturing the stream");
+    if (S->scratch) {
+        cudaFree(S->scratch);
+        S->scratch = nullptr;
+        S->scratch_bytes = 0;
+    }
+    SF_CK(cudaMalloc(&S->scratch, bytes), "scratch allocation");
+    S->scratch_bytes = bytes;
+    *out = S->scratch;
+    return SF_OK;
+}
+
+int occupancy(int mode, int dtype, int lpr) {
+    static std::mutex mu;
+    static int cache[M_COUNT][2][6] = {};
+    int li = 0;
+    while ((1 << li) < lpr) ++li;
+    std::lock_guard<std::mutex> lk(mu);
+    int &c = cache[mode][dtype][li];
+    if (!c) {
+        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr);
+        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) c = occupancy_adj(mode, dtype, lpr);
+        else c = occupancy_pair(mode, dtype, lpr);
+    }
+    return c;
+}
+
+sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int k, ExecArgs &a, cudaStream_t s) {
+    const int kt = S->kt ? std::min(S->kt, 32) : std::min(pow2_ceil(k), 32);
+    const int lpr = std::max(S->lpr, kt);
+    a.order = d.order;
+    a.part_ptr = d.part_ptr;
+    a.n_parts = d.n_parts;
+    a.n = S->n;
+    a.k = k;
+    a.kt = kt;
+    a.flags = d.flags;
+    a.st = d.st;
+    a.timeout_ns = S->timeout_ns;
+    a.Lrp = S->L.rowptr;
+    a.Lci = S->L.colidx;
+    a.Mrp = S->hasM ? S->M.rowptr : nullptr;
+    a.Mci = S->hasM ? S->M.colidx : nullptr;
+    a.LTrp = S->LT.t.rowptr;
+    a.LTci = S->LT.t.colidx;
+    a.LTperm = S->LT.perm;
+    a.MTrp = S->hasMT ? S->MT.t.rowptr : nullptr;
+    a.MTci = S->hasMT ? S->MT.t.colidx : nullptr;
+    a.MTperm = S->hasMT ? S->MT.perm : nullptr;
+    const int dtype = dt == SF_F64 ? 0 : 1;
+    const long long warps_wanted = d.n_parts;
+    long long blocks = (long long)occupancy(mode, dtype, lpr) * S->sms;
+    blocks = std::min<long long>(blocks, (warps_wanted + 7) / 8);
+    blocks = std::max<long long>(blocks, 1);
+    cudaError_t e;
+    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, (int)blocks, s, a);
+    else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) e = launch_exec_adj(mode, dtype, lpr, (int)blocks, s, a);
+    else e = launch_exec_pair(mode, dtype, lpr, (int)blocks, s, a);
+    if (e != cudaSuccess) return from_cuda(e, "executor launch");
+    return SF_OK;
+}
+
+}  // namespace
+
+// =========================================================================== ABI
+SF_API sf_status sf_inspect(sf_pair pair, const sf_csr *L, const sf_csr *M, const sf_options *opt, void *stream,
+                            sf_schedule **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) return fail(SF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!pair_valid(pair)) return fail(SF_ERR_INVALID_ARG, "unknown pair %d", (int)pair);
+    sf_status st = validate_options(opt);
+    if (st != SF_OK) return st;
+    sf_options o = opt ? *opt : sf_options{};
+    if ((o.flags & SF_WANT_ADJOINT) && pair != SF_TRSV_SPMV && pair != SF_SPMV_TRSV)
+        return fail(SF_ERR_UNSUPPORTED, "adjoint schedules exist for SF_TRSV_SPMV and SF_SPMV_TRSV only");
+    if ((st = check_csr_args(L, "L", true)) != SF_OK) return st;
+    if (pair_has_M(pair)) {
+        if ((st = check_csr_args(M, "M", true)) != SF_OK) return st;
+        if (M->n_rows != L->n_rows) return fail(SF_ERR_INVALID_ARG, "M must be n x n with n = L.n_rows");
+    } else if (M) {
+        return fail(SF_ERR_INVALID_ARG, "M must be NULL for this pair");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sf_schedule *S = new_schedule(pair);
+    if (!S) return fail(SF_ERR_OOM, "host allocation failed");
+    S->n = L->n_rows;
+    if ((st = copy_pattern(S, L, S->L, s)) != SF_OK) { delete S; return st; }
+    if (pair_has_M(pair)) {
+        S->hasM = true;
+        if ((st = copy_pattern(S, M, S->M, s)) != SF_OK) { delete S; return st; }
+    }
+    return finish_inspect(S, o, s, out, t0);
+}
+
+SF_API sf_status sf_inspect_batched(sf_pair pair, int32_t count, const sf_csr *Ls, const sf_csr *Ms,
+                                    const sf_options *opt, void *stream, sf_schedule **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) return fail(SF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!pair_valid(pair)) return fail(SF_ERR_INVALID_ARG, "unknown pair %d", (int)pair);
+    if (count < 1 || !Ls) return fail(SF_ERR_INVALID_ARG, "need count >= 1 instances");
+    if (pair_has_M(pair) && !Ms) return fail(SF_ERR_INVALID_ARG, "Ms is NULL");
+    sf_status st = validate_options(opt);
+    if (st != SF_OK) return st;
+    sf_options o = opt ? *opt : sf_options{};
+    if ((o.flags & SF_WANT_ADJOINT) && pair != SF_TRSV_SPMV && pair != SF_SPMV_TRSV)
+        return fail(SF_ERR_UNSUPPORTED, "adjoint schedules exist for SF_TRSV_SPMV and SF_SPMV_TRSV only");
+    long long n = 0, nnzL = 0, nnzM = 0;
+    std::vector<InstDesc> dl((size_t)count), dm(pair_has_M(pair) ? (size_t)count : 0);
+    for (int t = 0; t < count; ++t) {
+        char nm[32];
+        snprintf(nm, sizeof nm, "L[%d]", t);
+        if ((st = check_csr_args(&Ls[t], nm, true)) != SF_OK) return st;
+        if (pair_has_M(pair)) {
+            snprintf(nm, sizeof nm, "M[%d]", t);
+            if ((st = check_csr_args(&Ms[t], nm, true)) != SF_OK) return st;
+            if (Ms[t].n_rows != Ls[t].n_rows) return fail(SF_ERR_INVALID_ARG, "M[%d] size differs from L[%d]", t, t);
+            dm[t] = InstDesc{Ms[t].rowptr, Ms[t].colidx, Ms[t].n_rows, (int)n, (int)Ms[t].nnz, (int)nnzM};
+            nnzM += Ms[t].nnz;
+        }
+        dl[t] = InstDesc{Ls[t].rowptr, Ls[t].colidx, Ls[t].n_rows, (int)n, (int)Ls[t].nnz, (int)nnzL};
+        n += Ls[t].n_rows;
+        nnzL += Ls[t].nnz;
+        if (n >= (1LL << 31) - 1 || nnzL >= (1LL << 31) || nnzM >= (1LL << 31))
+            return fail(SF_ERR_INVALID_ARG, "batched total size exceeds int32 indexing");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sf_schedule *S = new_schedule(pair);
+    if (!S) return fail(SF_ERR_OOM, "host allocation failed");
+    S->n = (int)n;
+    S->instances = count;
+    Arena tmp;
+    auto alloc_csr = [&](DevCsr &d, long long nnz) {
+        d.n_rows = d.n_cols = (int)n;
+        d.nnz = nnz;
+        d.rowptr = (int *)S->keep.alloc(sizeof(int) * (size_t)(n + 1));
+        d.colidx = (int *)S->keep.alloc(sizeof(int) * (size_t)std::max<long long>(nnz, 1));
+        return d.rowptr && d.colidx;
+    };
+    if (!alloc_csr(S->L, nnzL)) { delete S; return fail(SF_ERR_OOM, "batched patterns: out of device memory"); }
+    cudaError_t e = concat_patterns(dl, S->L.rowptr, S->L.colidx, nnzL, (int)n, s, tmp);
+    if (e != cudaSuccess) { delete S; return from_cuda(e, "batched concatenation"); }
+    if (pair_has_M(pair)) {
+        S->hasM = true;
+        if (!alloc_csr(S->M, nnzM)) { delete S; return fail(SF_ERR_OOM, "batched patterns: out of device memory"); }
+        e = concat_patterns(dm, S->M.rowptr, S->M.colidx, nnzM, (int)n, s, tmp);
+        if (e != cudaSuccess) { delete S; return from_cuda(e, "batched concatenation"); }
+    }
+    return finish_inspect(S, o, s, out, t0);
+}
+
+SF_API sf_status sf_execute(const sf_schedule *S, sf_dtype dt, int32_t k, const void *L_vals, const void *M_vals,
+                            const void *x_in, const void *b, void *y, void *x_save, void *stream) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (dt != SF_F64 && dt != SF_F32) return fail(SF_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
+    if (k < 1 || k > 1024) return fail(SF_ERR_INVALID_ARG, "k must be in [1, 1024]");
+    if (!L_vals) return fail(SF_ERR_INVALID_ARG, "L_vals is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = dt == SF_F64 ? 8 : 4;
+    ExecArgs a{};
+    a.Lv = L_vals;
+    a.Mv = M_vals;
+    a.xin = x_in;
+    a.b = b;
+    a.y = y;
+    a.xs = x_save;
+    int mode = 0;
+    switch (S->pair) {
+        case SF_TRSV_SPMV:
+            if (!M_vals || !b || !y) return fail(SF_ERR_INVALID_ARG, "SF_TRSV_SPMV needs M_vals, b and y");
+            if (x_in) return fail(SF_ERR_INVALID_ARG, "x_in must be NULL for SF_TRSV_SPMV");
+            mode = M_TRSV_SPMV;
+            if (!x_save) {
+                sf_status st = get_scratch(S, (size_t)S->n * k * es, s, &a.xs);
+                if (st != SF_OK) return st;
+            }
+            break;
+        case SF_SPMV_TRSV:
+            if (!M_vals || !x_in || !b || !y) return fail(SF_ERR_INVALID_ARG, "SF_SPMV_TRSV needs M_vals, x_in, b and y");
+            mode = M_SPMV_TRSV;
+            break;
+        case SF_IC0_TRSV:
+            if (!b || !y) return fail(SF_ERR_INVALID_ARG, "SF_IC0_TRSV needs b and y");
+            if (M_vals || x_in) return fail(SF_ERR_INVALID_ARG, "M_vals and x_in must be NULL for SF_IC0_TRSV");
+            mode = M_IC0_TRSV;
+            if (!x_save) {
+                sf_status st = get_scratch(S, (size_t)S->L.nnz * es, s, &a.xs);
+                if (st != SF_OK) return st;
+            }
+            break;
+        case SF_TRSV:
+            if (!b || !y) return fail(SF_ERR_INVALID_ARG, "SF_TRSV needs b and y");
+            if (M_vals || x_in) return fail(SF_ERR_INVALID_ARG, "M_vals and x_in must be NULL for SF_TRSV");
+            mode = M_TRSV;
+            break;
+        case SF_IC0:
+            if (!x_save) return fail(SF_ERR_INVALID_ARG, "SF_IC0 needs x_save (the factor values)");
+            mode = M_IC0;
+            break;
+    }
+    return launch(S, S->fwd, mode, dt, k, a, s);
+}
+
+SF_API sf_status sf_adjoint(const sf_schedule *S, sf_dtype dt, int32_t k, const void *L_vals, const void *M_vals,
+                            const void *x_in, const void *saved, const void *gy, void *gb, void *gx_in,
+                            void *gL_vals, void *gM_vals, void *stream) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (dt != SF_F64 && dt != SF_F32) return fail(SF_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
+    if (k < 1 || k > 1024) return fail(SF_ERR_INVALID_ARG, "k must be in [1, 1024]");
+    if (S->pair != SF_TRSV_SPMV && S->pair != SF_SPMV_TRSV)
+        return fail(SF_ERR_UNSUPPORTED, "adjoints exist for SF_TRSV_SPMV and SF_SPMV_TRSV only");
+    if (!S->adj.present) return fail(SF_ERR_UNSUPPORTED, "schedule was inspected without SF_WANT_ADJOINT");
+    if (!L_vals || !M_vals || !gy || !gb) return fail(SF_ERR_INVALID_ARG, "L_vals, M_vals, gy and gb are required");
+    ExecArgs a{};
+    a.Lv = L_vals;
+    a.Mv = M_vals;
+    a.xin = x_in;
+    a.saved = saved;
+    a.gy = gy;
+    a.gb = gb;
+    a.gx = gx_in;
+    a.gL = gL_vals;
+    a.gM = gM_vals;
+    int mode;
+    if (S->pair == SF_TRSV_SPMV) {
+        if (gx_in || x_in) return fail(SF_ERR_INVALID_ARG, "x_in and gx_in must be NULL for SF_TRSV_SPMV");
+        if ((gL_vals || gM_vals) && !saved) return fail(SF_ERR_INVALID_ARG, "value gradients need saved = x");
+        mode = M_ADJ_TRSV_SPMV;
+    } else {
+        if (gL_vals && !saved) return fail(SF_ERR_INVALID_ARG, "gL_vals needs saved = z");
+        if (gM_vals && !x_in) return fail(SF_ERR_INVALID_ARG, "gM_vals (gradient of A) needs x_in");
+        mode = M_ADJ_SPMV_TRSV;
+    }
+    return launch(S, S->adj, mode, dt, k, a, (cudaStream_t)stream);
+}
+
+SF_API sf_status sf_spmv(sf_dtype dt, int32_t k, const sf_csr *M, const void *M_vals, const void *x, const void *b,
+                         void *y, void *stream) {
+    if (dt != SF_F64 && dt != SF_F32) return fail(SF_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
+    if (k < 1 || k > 1024) return fail(SF_ERR_INVALID_ARG, "k must be in [1, 1024]");
+    sf_status st = check_csr_args(M, "M", false);
+    if (st != SF_OK) return st;
+    if (!M_vals || !x || !y) return fail(SF_ERR_INVALID_ARG, "M_vals, x and y are required");
+    const long long mean = std::max<long long>(1, (M->nnz + M->n_rows - 1) / M->n_rows);
+    const int kt = std::min(pow2_ceil(k), 32);
+    const int lpr = std::max(kt, std::min(32, pow2_ceil((mean + 1) / 2)));
+    cudaError_t e = launch_spmv(dt == SF_F64 ? 0 : 1, lpr, kt, M->n_rows, k, M->rowptr, M->colidx, M_vals, x, b, y,
+                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return from_cuda(e, "spmv launch");
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_check(const sf_schedule *S, void *stream, int32_t *row) {
+    if (row) *row = -1;
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    SF_CK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+    const Dir *dirs[2] = {&S->fwd, &S->adj};
+    sf_status result = SF_OK;
+    for (const Dir *d : dirs) {
+        if (!d->present) continue;
+        ExecState h;
+        SF_CK(cudaMemcpy(&h, d->st, sizeof(ExecState), cudaMemcpyDeviceToHost), "state readback");
+        if (h.err_code && result == SF_OK) {
+            result = (sf_status)h.err_code;
+            if (row) *row = h.err_row;
+            fail(result, "%s pass: %s at row %d", d == &S->fwd ? "forward" : "adjoint",
+                 sf_status_string(result), h.err_row);
+        }
+        if (h.err_code) {
+            const unsigned z[2] = {0u, 0u};
+            SF_CK(cudaMemcpy(&d->st->err_code, z, sizeof z, cudaMemcpyHostToDevice), "state reset");
+        }
+    }
+    return result;
+}
+
+namespace {
+sf_status validate_dir(const sf_schedule *S, const Dir &d, const std::vector<int> &Lrp, const std::vector<int> &Lci,
+                       const std::vector<int> &Mrp, const std::vector<int> &Mci) {
+    const long long nv = d.nv;
+    const int n = S->n;
+    std::vector<int> order((size_t)nv), pp((size_t)d.n_parts + 1);
+    SF_CK(cudaMemcpy(order.data(), d.order, sizeof(int) * nv, cudaMemcpyDeviceToHost), "validate");
+    SF_CK(cudaMemcpy(pp.data(), d.part_ptr, sizeof(int) * (d.n_parts + 1), cudaMemcpyDeviceToHost), "validate");
+    std::vector<long long> pos((size_t)nv, -1);
+    for (long long q = 0; q < nv; ++q) {
+        const unsigned o = (unsigned)order[q];
+        const long long v = (long long)(o >> 31) * n + (o & 0x7fffffffu);
+        if ((o & 0x7fffffffu) >= (unsigned)n || v >= nv || pos[v] >= 0)
+            return fail(SF_ERR_BAD_PATTERN, "order is not a permutation (position %lld)", q);
+        pos[v] = q;
+    }
+    const bool fwd = d.kind == K_SEP || d.kind == K_PAIRED;
+    for (int i = 0; i < n; ++i) {
+        for (int e = Lrp[i]; e < Lrp[i + 1]; ++e) {
+            const int j = Lci[e];
+            if (j == i) continue;
+            const bool ok = fwd ? pos[j] < pos[i] : pos[i] < pos[j];
+            if (!ok) return fail(SF_ERR_BAD_PATTERN, "DAG edge of L(%d,%d) violated", i, j);
+        }
+        if (d.kind == K_SEP)
+            for (int e = Mrp[i]; e < Mrp[i + 1]; ++e)
+                if (!(pos[Mci[e]] < pos[(long long)n + i])) return fail(SF_ERR_BAD_PATTERN, "F edge (%d,%d) violated", i, Mci[e]);
+        if (d.kind == K_SEP_T)
+            for (int e = Mrp[i]; e < Mrp[i + 1]; ++e)
+                if (!(pos[i] < pos[(long long)n + Mci[e]]))
+                    return fail(SF_ERR_BAD_PATTERN, "adjoint F edge (%d,%d) violated", i, Mci[e]);
+    }
+    if (pp[0] != 0 || pp[d.n_parts] != nv) return fail(SF_ERR_BAD_PATTERN, "partitions do not cover the order");
+    for (int p = 0; p < d.n_parts; ++p)
+        if (pp[p + 1] <= pp[p]) return fail(SF_ERR_BAD_PATTERN, "empty or decreasing partition %d", p);
+    return SF_OK;
+}
+}  // namespace
+
+SF_API sf_status sf_validate(const sf_schedule *S) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    const int n = S->n;
+    std::vector<int> Lrp((size_t)n + 1), Lci((size_t)std::max<long long>(S->L.nnz, 1)), Mrp, Mci;
+    SF_CK(cudaMemcpy(Lrp.data(), S->L.rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost), "validate");
+    SF_CK(cudaMemcpy(Lci.data(), S->L.colidx, sizeof(int) * S->L.nnz, cudaMemcpyDeviceToHost), "validate");
+    if (S->hasM) {
+        Mrp.resize((size_t)n + 1);
+        Mci.resize((size_t)std::max<long long>(S->M.nnz, 1));
+        SF_CK(cudaMemcpy(Mrp.data(), S->M.rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost), "validate");
+        SF_CK(cudaMemcpy(Mci.data(), S->M.colidx, sizeof(int) * S->M.nnz, cudaMemcpyDeviceToHost), "validate");
+    }
+    sf_status st = validate_dir(S, S->fwd, Lrp, Lci, Mrp, Mci);
+    if (st != SF_OK || !S->adj.present) return st;
+    return validate_dir(S, S->adj, Lrp, Lci, Mrp, Mci);
+}
+
+SF_API sf_status sf_schedule_info(const sf_schedule *S, int32_t *depth, int32_t *n_parts, int64_t *n_items) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (depth) *depth = S->fwd.depth;
+    if (n_parts) *n_parts = S->fwd.n_parts;
+    if (n_items) *n_items = S->fwd.nv;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
+    if (!S || !info) return fail(SF_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof *info);
+    info->pair = S->pair;
+    info->n = S->n;
+    info->instances = S->instances;
+    info->depth = S->fwd.depth;
+    info->n_parts = S->fwd.n_parts;
+    info->n_items = S->fwd.nv;
+    if (S->adj.present) {
+        info->adj_depth = S->adj.depth;
+        info->adj_n_parts = S->adj.n_parts;
+        info->adj_n_items = S->adj.nv;
+        info->adj_part_cost_target = S->adj.C;
+    }
+    info->lanes_per_row = S->lpr;
+    info->rhs_tile = S->kt;
+    info->part_cost_target = S->fwd.C;
+    info->packing = S->packing;
+    info->reuse_ratio = S->reuse;
+    info->inspect_ms = S->inspect_ms;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_export(const sf_schedule *S, int32_t which, int32_t *level, int32_t *order,
+                                    int32_t *part_ptr) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which != 0 && which != 1) return fail(SF_ERR_INVALID_ARG, "which must be 0 or 1");
+    const Dir &d = which ? S->adj : S->fwd;
+    if (!d.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    if (level) SF_CK(cudaMemcpy(level, d.level, sizeof(int) * d.nv, cudaMemcpyDeviceToHost), "export");
+    if (order) SF_CK(cudaMemcpy(order, d.order, sizeof(int) * d.nv, cudaMemcpyDeviceToHost), "export");
+    if (part_ptr) SF_CK(cudaMemcpy(part_ptr, d.part_ptr, sizeof(int) * (d.n_parts + 1), cudaMemcpyDeviceToHost), "export");
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_launch(sf_schedule *S, int32_t lanes_per_row, int32_t rhs_tile) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (lanes_per_row && !is_pow2_upto32(lanes_per_row)) return fail(SF_ERR_INVALID_ARG, "bad lanes_per_row");
+    if (rhs_tile && !is_pow2_upto32(rhs_tile)) return fail(SF_ERR_INVALID_ARG, "bad rhs_tile");
+    const int lpr = lanes_per_row ? lanes_per_row : S->lpr;
+    const int kt = rhs_tile ? rhs_tile : S->kt;
+    if (kt > lpr) return fail(SF_ERR_INVALID_ARG, "rhs_tile must not exceed lanes_per_row");
+    S->lpr = lpr;
+    S->kt = kt;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_timeout(sf_schedule *S, uint64_t timeout_ns) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    S->timeout_ns = timeout_ns ? timeout_ns : 2000000000ull;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_debug_swap(sf_schedule *S, int64_t q1, int64_t q2) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (q1 < 0 || q2 < 0 || q1 >= S->fwd.nv || q2 >= S->fwd.nv) return fail(SF_ERR_INVALID_ARG, "position out of range");
+    int a = 0, b = 0;
+    SF_CK(cudaMemcpy(&a, S->fwd.order + q1, sizeof(int), cudaMemcpyDeviceToHost), "swap");
+    SF_CK(cudaMemcpy(&b, S->fwd.order + q2, sizeof(int), cudaMemcpyDeviceToHost), "swap");
+    SF_CK(cudaMemcpy(S->fwd.order + q1, &b, sizeof(int), cudaMemcpyHostToDevice), "swap");
+    SF_CK(cudaMemcpy(S->fwd.order + q2, &a, sizeof(int), cudaMemcpyHostToDevice), "swap");
+    return SF_OK;
+}
+
+SF_API void sf_schedule_destroy(sf_schedule *S) {
+    if (!S) return;
+    if (S->scratch) cudaFree(S->scratch);
+    delete S;
+}
+
+SF_API const char *sf_status_string(sf_status s) {
+    switch (s) {
+        case SF_OK: return "SF_OK";
+        case SF_ERR_INVALID_ARG: return "SF_ERR_INVALID_ARG";
+        case SF_ERR_BAD_PATTERN: return "SF_ERR_BAD_PATTERN";
+        case SF_ERR_CUDA: return "SF_ERR_CUDA";
+        case SF_ERR_OOM: return "SF_ERR_OOM";
+        case SF_ERR_TIMEOUT: return "SF_ERR_TIMEOUT";
+        case SF_ERR_BREAKDOWN: return "SF_ERR_BREAKDOWN";
+        case SF_ERR_NONFINITE: return "SF_ERR_NONFINITE";
+        case SF_ERR_UNSUPPORTED: return "SF_ERR_UNSUPPORTED";
+    }
+    return "unknown sf_status";
+}
+
+SF_API sf_status sf_last_error_detail(char *buf, size_t len) {
+    if (!buf || len == 0) return SF_ERR_INVALID_ARG;
+    snprintf(buf, len, "%s", g_detail);
+    return SF_OK;
+}

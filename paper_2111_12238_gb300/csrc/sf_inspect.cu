@@ -1,0 +1,612 @@
+// GPU inspector (§2.2, §3): pattern checks, CSR transposes (successor lists of the DAGs),
+// wavefront levels of the joint DAG by parallel Kahn peeling, the linear order by
+// (level, kernel, row) and the cut of that order into cost-balanced partitions.
+//
+// Building blocks are hand-written: a three-phase exclusive scan, a stable LSD radix sort
+// (8-bit digits, per-block histograms, in-tile ranking with warp match), a count/scan/
+// sort transpose and a cooperative persistent Kahn kernel with a bounded grid barrier.
+#include <vector>
+
+#include "sf_inspect.cuh"
+
+namespace sf {
+
+// ------------------------------------------------------------------------------ arena
+void *Arena::alloc(size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        oom = true;
+        return nullptr;
+    }
+    ptrs.push_back(p);
+    return p;
+}
+Arena::~Arena() {
+    for (void *p : ptrs) cudaFree(p);
+}
+
+static inline unsigned grid_for(long long n, int threads, long long cap = 1 << 20) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------------------------ scan
+constexpr int kScanT = 256, kScanI = 8, kScanTile = kScanT * kScanI;
+
+template <typename T>
+__device__ T block_excl_scan(T v, T *total) {
+    __shared__ T wtot[kScanT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    T inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += t;
+    }
+    if (lane == 31) wtot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T w = lane < kScanT / 32 ? wtot[lane] : T(0);
+#pragma unroll
+        for (int off = 1; off < kScanT / 32; off <<= 1) {
+            const T t = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += t;
+        }
+        if (lane < kScanT / 32) wtot[lane] = w;
+    }
+    __syncthreads();
+    *total = wtot[kScanT / 32 - 1];
+    return (wid > 0 ? wtot[wid - 1] : T(0)) + inc - v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanT) k_scan_reduce(const T *__restrict__ in, long long n, T *__restrict__ sums) {
+    const long long base = (long long)blockIdx.x * kScanTile;
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < kScanI; ++i) {
+        const long long idx = base + i * kScanT + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    T tot;
+    block_excl_scan<T>(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// exclusive scan of sums[0..nb) in place, one block
+template <typename T>
+__global__ void __launch_bounds__(kScanT) k_scan_top(T *sums, long long nb) {
+    T carry = T(0);
+    for (long long c0 = 0; c0 < nb; c0 += kScanTile) {
+        T loc[kScanI];
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < kScanI; ++i) {
+            const long long idx = c0 + (long long)threadIdx.x * kScanI + i;
+            loc[i] = idx < nb ? sums[idx] : T(0);
+            s += loc[i];
+        }
+        T tot;
+        T pre = block_excl_scan<T>(s, &tot) + carry;
+#pragma unroll
+        for (int i = 0; i < kScanI; ++i) {
+            const long long idx = c0 + (long long)threadIdx.x * kScanI + i;
+            if (idx < nb) sums[idx] = pre;
+            pre += loc[i];
+        }
+        carry += tot;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanT) k_scan_down(const T *__restrict__ in, T *__restrict__ out, long long n,
+                                                      const T *__restrict__ sums) {
+    const long long base = (long long)blockIdx.x * kScanTile;
+    T loc[kScanI];
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < kScanI; ++i) {
+        const long long idx = base + (long long)threadIdx.x * kScanI + i;
+        loc[i] = idx < n ? in[idx] : T(0);
+        s += loc[i];
+    }
+    T tot;
+    T pre = block_excl_scan<T>(s, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanI; ++i) {
+        const long long idx = base + (long long)threadIdx.x * kScanI + i;
+        if (idx < n) out[idx] = pre;
+        pre += loc[i];
+        if (idx == n - 1) out[n] = pre;
+    }
+}
+
+template <typename T>
+__global__ void k_set_zero1(T *out) { out[0] = T(0); }
+
+template <typename T>
+cudaError_t scan_excl(const T *in, T *out, long long n, cudaStream_t s, Arena &ar) {
+    if (n <= 0) {
+        k_set_zero1<T><<<1, 1, 0, s>>>(out);
+        return cudaGetLastError();
+    }
+    const long long nb = (n + kScanTile - 1) / kScanTile;
+    T *sums = (T *)ar.alloc(sizeof(T) * nb);
+    if (!sums) return cudaErrorMemoryAllocation;
+    k_scan_reduce<T><<<(unsigned)nb, kScanT, 0, s>>>(in, n, sums);
+    k_scan_top<T><<<1, kScanT, 0, s>>>(sums, nb);
+    k_scan_down<T><<<(unsigned)nb, kScanT, 0, s>>>(in, out, n, sums);
+    return cudaGetLastError();
+}
+template cudaError_t scan_excl<int>(const int *, int *, long long, cudaStream_t, Arena &);
+template cudaError_t scan_excl<long long>(const long long *, long long *, long long, cudaStream_t, Arena &);
+
+// ------------------------------------------------------------------------------ radix sort
+constexpr int kRsT = 256, kRsR = 16, kRsTile = kRsT * kRsR;
+
+__global__ void __launch_bounds__(kRsT) k_radix_hist(const unsigned *__restrict__ keys, long long n, int shift,
+                                                     int *__restrict__ hist, int nb) {
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRsTile;
+#pragma unroll 4
+    for (int r = 0; r < kRsR; ++r) {
+        const long long idx = base + r * kRsT + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * nb + blockIdx.x] = (int)h[threadIdx.x];
+}
+
+// Stable scatter: element order inside a tile is (round, warp, lane); the rank of an
+// element among equal digits is the count of earlier rounds, earlier warps of this round
+// and lower lanes of this warp.
+__global__ void __launch_bounds__(kRsT) k_radix_scatter(const unsigned *__restrict__ kin,
+                                                        const unsigned *__restrict__ vin,
+                                                        unsigned *__restrict__ kout, unsigned *__restrict__ vout,
+                                                        long long n, int shift, const int *__restrict__ hscan,
+                                                        int nb) {
+    __shared__ unsigned run[256];
+    __shared__ unsigned wcnt[kRsT / 32][256];
+    __shared__ unsigned gofs[256];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    gofs[tid] = (unsigned)hscan[(long long)tid * nb + blockIdx.x];
+    run[tid] = 0;
+#pragma unroll
+    for (int w = 0; w < kRsT / 32; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsR; ++r) {
+        const long long idx = base + r * kRsT + tid;
+        const bool valid = idx < n;
+        const unsigned key = valid ? kin[idx] : 0u;
+        const unsigned d = (key >> shift) & 255u;
+        const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned off = run[d] + rank;
+            for (int w = 0; w < wid; ++w) off += wcnt[w][d];
+            const unsigned pos = gofs[d] + off;
+            kout[pos] = key;
+            vout[pos] = vin[idx];
+        }
+        __syncthreads();
+        unsigned t = 0;
+#pragma unroll
+        for (int w = 0; w < kRsT / 32; ++w) {
+            t += wcnt[w][tid];
+            wcnt[w][tid] = 0;
+        }
+        run[tid] += t;
+        __syncthreads();
+    }
+}
+
+int bits_for(unsigned long long maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+cudaError_t radix_sort_pairs(unsigned *keys, unsigned *vals, long long n, int bits, cudaStream_t s, Arena &ar) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    const int nb = (int)((n + kRsTile - 1) / kRsTile);
+    unsigned *k2 = (unsigned *)ar.alloc(sizeof(unsigned) * n);
+    unsigned *v2 = (unsigned *)ar.alloc(sizeof(unsigned) * n);
+    int *hist = (int *)ar.alloc(sizeof(int) * 256 * (size_t)nb);
+    int *hscan = (int *)ar.alloc(sizeof(int) * (256 * (size_t)nb + 1));
+    if (!k2 || !v2 || !hist || !hscan) return cudaErrorMemoryAllocation;
+    unsigned *ki = keys, *vi = vals, *ko = k2, *vo = v2;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<nb, kRsT, 0, s>>>(ki, n, shift, hist, nb);
+        cudaError_t e = scan_excl<int>(hist, hscan, 256LL * nb, s, ar);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<nb, kRsT, 0, s>>>(ki, vi, ko, vo, n, shift, hscan, nb);
+        unsigned *t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    if (ki != keys) {
+        cudaMemcpyAsync(keys, ki, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, vi, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ patterns
+// First violation per matrix as (code << 32 | row), minimised over rows.
+__device__ __forceinline__ void report_pattern(unsigned long long *status, unsigned code, int row) {
+    atomicMin(status, ((unsigned long long)code << 32) | (unsigned)row);
+}
+
+__global__ void k_check_csr(int n_rows, int n_cols, long long nnz, const int *__restrict__ rp,
+                            const int *__restrict__ ci, int lower, unsigned long long *status) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    if (i == 0 && rp[0] != 0) report_pattern(status, PAT_ROWPTR0, 0);
+    if (i == n_rows - 1 && rp[n_rows] != nnz) report_pattern(status, PAT_NNZ, (int)i);
+    const int a = rp[i], b = rp[i + 1];
+    if (b < a || a < 0 || b > nnz) {
+        report_pattern(status, PAT_ROWPTR, (int)i);
+        return;
+    }
+    for (int e = a; e < b; ++e) {
+        const int c = ci[e];
+        if (c < 0 || c >= n_cols) { report_pattern(status, PAT_COL_RANGE, (int)i); return; }
+        if (e > a && ci[e - 1] >= c) { report_pattern(status, PAT_UNSORTED, (int)i); return; }
+    }
+    if (lower && (b == a || ci[b - 1] != i)) report_pattern(status, PAT_DIAG, (int)i);
+}
+
+__global__ void k_row_of(int n, const int *__restrict__ rp, int *__restrict__ row_of) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = (int)i;
+}
+
+__global__ void k_count_cols(long long nnz, const int *__restrict__ ci, int *__restrict__ cnt) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[e]], 1);
+}
+
+__global__ void k_iota(long long n, unsigned *__restrict__ v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = (unsigned)i;
+}
+
+__global__ void k_gather_rows(long long nnz, const unsigned *__restrict__ perm, const int *__restrict__ row_of,
+                              int *__restrict__ tci, int *__restrict__ tperm) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x) {
+        const unsigned e = perm[t];
+        tci[t] = row_of[e];
+        tperm[t] = (int)e;
+    }
+}
+
+cudaError_t transpose_csr(const DevCsr &src, DevCsrT &dst, cudaStream_t s, Arena &ar, Arena &keep) {
+    const long long nnz = src.nnz;
+    dst.t.n_rows = src.n_cols;
+    dst.t.n_cols = src.n_rows;
+    dst.t.nnz = nnz;
+    dst.t.rowptr = (int *)keep.alloc(sizeof(int) * ((size_t)src.n_cols + 1));
+    dst.t.colidx = (int *)keep.alloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    dst.perm = (int *)keep.alloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    int *cnt = (int *)ar.alloc(sizeof(int) * ((size_t)src.n_cols + 1));
+    int *row_of = (int *)ar.alloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    unsigned *keys = (unsigned *)ar.alloc(sizeof(unsigned) * (size_t)(nnz > 0 ? nnz : 1));
+    unsigned *vals = (unsigned *)ar.alloc(sizeof(unsigned) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!dst.t.rowptr || !dst.t.colidx || !dst.perm || !cnt || !row_of || !keys || !vals)
+        return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)src.n_cols + 1), s);
+    if (nnz > 0) {
+        k_count_cols<<<grid_for(nnz, 256, 4096), 256, 0, s>>>(nnz, src.colidx, cnt);
+        k_row_of<<<grid_for(src.n_rows, 256), 256, 0, s>>>(src.n_rows, src.rowptr, row_of);
+    }
+    cudaError_t e = scan_excl<int>(cnt, dst.t.rowptr, src.n_cols, s, ar);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0) {
+        cudaMemcpyAsync(keys, src.colidx, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s);
+        k_iota<<<grid_for(nnz, 256, 4096), 256, 0, s>>>(nnz, vals);
+        e = radix_sort_pairs(keys, vals, nnz, bits_for(src.n_cols > 0 ? (unsigned long long)src.n_cols - 1 : 0), s, ar);
+        if (e != cudaSuccess) return e;
+        k_gather_rows<<<grid_for(nnz, 256, 4096), 256, 0, s>>>(nnz, vals, row_of, dst.t.colidx, dst.perm);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------ Kahn
+// In-degree of every joint-DAG vertex: one count per edge of the successor lists.
+__global__ void k_indeg(int n1, const int *__restrict__ s1rp, const int *__restrict__ s1ci,
+                        const int *__restrict__ s2rp, const int *__restrict__ s2ci, int *__restrict__ indeg) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n1) return;
+    for (int e = s1rp[v]; e < s1rp[v + 1]; ++e) {
+        const int t = s1ci[e];
+        if (t != v) atomicAdd(&indeg[t], 1);
+    }
+    if (s2rp)
+        for (int e = s2rp[v]; e < s2rp[v + 1]; ++e) atomicAdd(&indeg[n1 + s2ci[e]], 1);
+}
+
+__global__ void k_sources(long long nv, const int *__restrict__ indeg, int *__restrict__ queue, KahnCtl *ctl) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool src = v < nv && indeg[v] == 0;
+    const unsigned m = __ballot_sync(0xffffffffu, src);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(&ctl->nsrc, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (src) queue[base + __popc(m & lanemask_lt())] = (int)v;
+}
+
+// Grid-wide barrier for a cooperative launch, bounded by a spin limit: returns false
+// (and sets ctl->err) if the other blocks do not arrive in time.
+__device__ bool grid_barrier(KahnCtl *ctl, unsigned nblocks, unsigned long long tmo) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire_u32(&ctl->bar_gen);
+        const unsigned arrived = atom_add_acq_rel_u32(&ctl->bar_count, 1u);
+        if (arrived == nblocks - 1u) {
+            st_relaxed_u32(&ctl->bar_count, 0u);
+            st_release_u32(&ctl->bar_gen, gen + 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned it = 0;
+            while (ld_acquire_u32(&ctl->bar_gen) == gen) {
+                if ((++it & 255u) == 0u && global_ns() - t0 > tmo) {
+                    atomicExch(&ctl->err, 1u);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Frontier peeling: round r owns the vertices whose last predecessor was removed in
+// round r-1 (its level is r); removing a vertex decrements its successors' in-degrees and
+// appends those that reach zero to the next frontier. Counters of the next frontier are
+// triple-buffered so that no block reads a count while another resets it.
+__global__ void __launch_bounds__(256) k_kahn(int n1, const int *__restrict__ s1rp, const int *__restrict__ s1ci,
+                                              const int *__restrict__ s2rp, const int *__restrict__ s2ci,
+                                              int *__restrict__ indeg, int *__restrict__ queue,
+                                              int *__restrict__ level, KahnCtl *ctl, unsigned long long tmo) {
+    const unsigned nblocks = gridDim.x;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    long long fs = 0, fe = (long long)ld_acquire_u32(&ctl->nsrc);
+    int round = 0;
+    while (fs < fe) {
+        unsigned *cnt = &ctl->cnt[round % 3];
+        for (long long idx = fs + gtid; idx < fe; idx += gstride) {
+            const int v = queue[idx];
+            level[v] = round;
+            if (v < n1) {
+                for (int e = s1rp[v]; e < s1rp[v + 1]; ++e) {
+                    const int t = s1ci[e];
+                    if (t == v) continue;
+                    if (atomicSub(&indeg[t], 1) == 1) queue[fe + atomicAdd(cnt, 1u)] = t;
+                }
+                if (s2rp)
+                    for (int e = s2rp[v]; e < s2rp[v + 1]; ++e) {
+                        const int t = n1 + s2ci[e];
+                        if (atomicSub(&indeg[t], 1) == 1) queue[fe + atomicAdd(cnt, 1u)] = t;
+                    }
+            }
+        }
+        if (gtid == 0) ctl->cnt[(round + 1) % 3] = 0u;
+        if (!grid_barrier(ctl, nblocks, tmo)) return;
+        const long long nf = (long long)ld_acquire_u32(cnt);
+        fs = fe;
+        fe += nf;
+        ++round;
+    }
+    if (gtid == 0) {
+        ctl->depth = (unsigned)round;
+        ctl->processed = (unsigned)fe;
+    }
+}
+
+cudaError_t kahn_levels(long long nv, int n1, const int *s1rp, const int *s1ci, const int *s2rp, const int *s2ci,
+                        int *level, int *depth_out, cudaStream_t s, Arena &ar, bool *timed_out) {
+    *timed_out = false;
+    int *indeg = (int *)ar.alloc(sizeof(int) * nv);
+    int *queue = (int *)ar.alloc(sizeof(int) * nv);
+    KahnCtl *ctl = (KahnCtl *)ar.alloc(sizeof(KahnCtl));
+    if (!indeg || !queue || !ctl) return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(indeg, 0, sizeof(int) * nv, s);
+    cudaMemsetAsync(ctl, 0, sizeof(KahnCtl), s);
+    k_indeg<<<grid_for(n1, 256), 256, 0, s>>>(n1, s1rp, s1ci, s2rp, s2ci, indeg);
+    k_sources<<<grid_for(nv, 256), 256, 0, s>>>(nv, indeg, queue, ctl);
+    int dev = 0, sms = 0, occ = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return cudaErrorNotSupported;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_kahn, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    long long want = (nv + 255) / 256;
+    long long blocks = (long long)sms * occ;
+    if (blocks > want) blocks = want;
+    if (blocks < 1) blocks = 1;
+    unsigned long long tmo = 5000000000ull;   // 5 s per barrier
+    void *args[] = {(void *)&n1, (void *)&s1rp, (void *)&s1ci, (void *)&s2rp, (void *)&s2ci, (void *)&indeg,
+                    (void *)&queue, (void *)&level, (void *)&ctl, (void *)&tmo};
+    e = cudaLaunchCooperativeKernel((const void *)k_kahn, dim3((unsigned)blocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    KahnCtl h;
+    e = cudaMemcpyAsync(&h, ctl, sizeof(KahnCtl), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (h.err) {
+        *timed_out = true;
+        return cudaSuccess;
+    }
+    if ((long long)h.processed != nv) return cudaErrorInvalidValue;   // a cycle: impossible for valid input
+    *depth_out = (int)h.depth;
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------ order, costs, cut
+__global__ void k_level_keys(long long nv, const int *__restrict__ level, unsigned *__restrict__ keys,
+                             unsigned *__restrict__ vals) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+        keys[v] = (unsigned)level[v];
+        vals[v] = (unsigned)v;
+    }
+}
+
+__global__ void k_encode_order(long long nv, int n1, const unsigned *__restrict__ vids, int *__restrict__ order) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
+        const unsigned v = vids[q];
+        order[q] = (int)(v < (unsigned)n1 ? v : ((v - (unsigned)n1) | 0x80000000u));
+    }
+}
+
+// c(v) of §3.1 (nonzeros touched by the iteration) + 1; formulas per `what`:
+// 0 SEP, 1 PAIRED_T, 2 SEP_T, 3 SpMV->SpTRSV, 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0.
+__global__ void k_costs(int what, int n, const int *__restrict__ Lrp, const int *__restrict__ Lci,
+                        const int *__restrict__ Mrp, const int *__restrict__ LTrp, const int *__restrict__ MTrp,
+                        int *__restrict__ cost) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nl = Lrp[i + 1] - Lrp[i];
+    const int nm = Mrp ? Mrp[i + 1] - Mrp[i] : 0;
+    const int cl = LTrp ? LTrp[i + 1] - LTrp[i] : 0;
+    const int cm = MTrp ? MTrp[i + 1] - MTrp[i] : 0;
+    int sj = 0;
+    if (what == 4 || what == 6)
+        for (int e = Lrp[i]; e < Lrp[i + 1] - 1; ++e) {
+            const int j = Lci[e];
+            sj += Lrp[j + 1] - Lrp[j];
+        }
+    switch (what) {
+        case 0: cost[i] = nl + 1; cost[n + i] = nm + 1; break;
+        case 1: cost[i] = cm + cl + nl + nm + 1; break;
+        case 2: cost[i] = cl + nl + nm + 1; cost[n + i] = cm + 1; break;
+        case 3: cost[i] = nm + nl + 1; break;
+        case 4: cost[i] = 2 * nl + sj + 1; break;
+        case 5: cost[i] = nl + 1; break;
+        default: cost[i] = nl + sj + 1; break;
+    }
+}
+
+__global__ void k_gather_cost(long long nv, int n1, const int *__restrict__ order, const int *__restrict__ cost,
+                              long long *__restrict__ cs) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
+        const unsigned o = (unsigned)order[q];
+        cs[q] = cost[(long long)(o >> 31) * n1 + (o & 0x7fffffffu)];
+    }
+}
+
+__global__ void k_cut_flags(long long nv, const long long *__restrict__ S, long long C, int *__restrict__ f) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x)
+        f[q] = (q == 0 || S[q] / C != S[q - 1] / C) ? 1 : 0;
+}
+
+__global__ void k_cut_scatter(long long nv, const int *__restrict__ f, const int *__restrict__ idx,
+                              int *__restrict__ part_ptr) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
+        if (f[q]) part_ptr[idx[q]] = (int)q;
+        if (q == 0) part_ptr[idx[nv]] = (int)nv;
+    }
+}
+
+cudaError_t build_order(long long nv, int n1, const int *level, int depth, int *order, cudaStream_t s, Arena &ar) {
+    unsigned *keys = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
+    unsigned *vals = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
+    if (!keys || !vals) return cudaErrorMemoryAllocation;
+    k_level_keys<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, level, keys, vals);
+    cudaError_t e = radix_sort_pairs(keys, vals, nv, bits_for(depth > 0 ? (unsigned long long)depth - 1 : 0), s, ar);
+    if (e != cudaSuccess) return e;
+    k_encode_order<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, n1, vals, order);
+    return cudaGetLastError();
+}
+
+cudaError_t vertex_costs(int what, int n, const DevCsr &L, const DevCsr *M, const DevCsrT *LT, const DevCsrT *MT,
+                         int *cost, cudaStream_t s) {
+    k_costs<<<grid_for(n, 256), 256, 0, s>>>(what, n, L.rowptr, L.colidx, M ? M->rowptr : nullptr,
+                                             LT ? LT->t.rowptr : nullptr, MT ? MT->t.rowptr : nullptr, cost);
+    return cudaGetLastError();
+}
+
+cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost, long long *S, long long *total,
+                         cudaStream_t s, Arena &ar) {
+    long long *cs = (long long *)ar.alloc(sizeof(long long) * nv);
+    if (!cs) return cudaErrorMemoryAllocation;
+    k_gather_cost<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, n1, order, cost, cs);
+    cudaError_t e = scan_excl<long long>(cs, S, nv, s, ar);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(total, S + nv, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t cut_partitions(long long nv, const long long *S, long long C, int *part_ptr_out_capacity_nv1,
+                           int *n_parts, cudaStream_t s, Arena &ar) {
+    int *f = (int *)ar.alloc(sizeof(int) * nv);
+    int *idx = (int *)ar.alloc(sizeof(int) * (nv + 1));
+    if (!f || !idx) return cudaErrorMemoryAllocation;
+    k_cut_flags<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, S, C, f);
+    cudaError_t e = scan_excl<int>(f, idx, nv, s, ar);
+    if (e != cudaSuccess) return e;
+    k_cut_scatter<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, f, idx, part_ptr_out_capacity_nv1);
+    e = cudaMemcpyAsync(n_parts, idx + nv, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+// ------------------------------------------------------------------------------ batching
+__global__ void k_concat(const InstDesc *__restrict__ d, int *__restrict__ rp_out, int *__restrict__ ci_out) {
+    const InstDesc in = d[blockIdx.y];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < in.n; i += (long long)gridDim.x * blockDim.x)
+        rp_out[in.row_off + i] = in.rowptr[i] + in.nnz_off;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < in.nnz; e += (long long)gridDim.x * blockDim.x)
+        ci_out[in.nnz_off + e] = in.colidx[e] + in.row_off;
+}
+
+cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci_out, long long total_nnz,
+                            int total_rows, cudaStream_t s, Arena &ar) {
+    if (h.empty()) return cudaErrorInvalidValue;
+    InstDesc *d = (InstDesc *)ar.alloc(sizeof(InstDesc) * h.size());
+    if (!d) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(InstDesc) * h.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    unsigned gy = (unsigned)h.size();
+    k_concat<<<dim3(64, gy), 256, 0, s>>>(d, rp_out, ci_out);
+    const int last = (int)total_nnz;
+    e = cudaMemcpyAsync(rp_out + total_rows, &last, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);   // `last` and `h` live on this stack frame
+}
+
+cudaError_t check_pattern(const DevCsr &m, int lower, unsigned long long *status_host, cudaStream_t s, Arena &ar) {
+    unsigned long long *st = (unsigned long long *)ar.alloc(sizeof(unsigned long long));
+    if (!st) return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(st, 0xff, sizeof(unsigned long long), s);
+    if (m.n_rows > 0)
+        k_check_csr<<<grid_for(m.n_rows, 256), 256, 0, s>>>(m.n_rows, m.n_cols, m.nnz, m.rowptr, m.colidx, lower, st);
+    cudaError_t e = cudaMemcpyAsync(status_host, st, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace sf

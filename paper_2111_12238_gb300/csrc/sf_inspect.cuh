@@ -1,0 +1,75 @@
+// Inspector building blocks (declarations).
+#pragma once
+
+#include <vector>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+// Device allocations that are released together (temporaries of one inspector call, or
+// the arrays a schedule owns).
+struct Arena {
+    std::vector<void *> ptrs;
+    bool oom = false;
+    void *alloc(size_t bytes);
+    ~Arena();
+};
+
+struct DevCsr {
+    int n_rows = 0, n_cols = 0;
+    long long nnz = 0;
+    int *rowptr = nullptr;
+    int *colidx = nullptr;
+};
+
+// Transposed pattern plus, per transposed entry, the index of that entry in the source
+// CSR (to read the source's values in transposed order).
+struct DevCsrT {
+    DevCsr t;
+    int *perm = nullptr;
+};
+
+struct KahnCtl {
+    unsigned cnt[3];
+    unsigned nsrc;
+    unsigned bar_count;
+    unsigned bar_gen;
+    unsigned err;
+    unsigned depth;
+    unsigned processed;
+};
+
+struct InstDesc {
+    const int *rowptr;
+    const int *colidx;
+    int n;
+    int row_off;
+    int nnz;
+    int nnz_off;
+};
+
+// pattern violation codes (high word of the status of k_check_csr)
+enum PatCode : unsigned {
+    PAT_ROWPTR0 = 1, PAT_NNZ = 2, PAT_ROWPTR = 3, PAT_COL_RANGE = 4, PAT_UNSORTED = 5, PAT_DIAG = 6
+};
+
+int bits_for(unsigned long long maxval);
+template <typename T>
+cudaError_t scan_excl(const T *in, T *out, long long n, cudaStream_t s, Arena &ar);
+cudaError_t radix_sort_pairs(unsigned *keys, unsigned *vals, long long n, int bits, cudaStream_t s, Arena &ar);
+cudaError_t check_pattern(const DevCsr &m, int lower, unsigned long long *status_host, cudaStream_t s, Arena &ar);
+cudaError_t transpose_csr(const DevCsr &src, DevCsrT &dst, cudaStream_t s, Arena &ar, Arena &keep);
+cudaError_t kahn_levels(long long nv, int n1, const int *s1rp, const int *s1ci, const int *s2rp, const int *s2ci,
+                        int *level, int *depth_out, cudaStream_t s, Arena &ar, bool *timed_out);
+cudaError_t build_order(long long nv, int n1, const int *level, int depth, int *order, cudaStream_t s, Arena &ar);
+cudaError_t vertex_costs(int what, int n, const DevCsr &L, const DevCsr *M, const DevCsrT *LT, const DevCsrT *MT,
+                         int *cost, cudaStream_t s);
+cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost, long long *S, long long *total,
+                         cudaStream_t s, Arena &ar);
+cudaError_t cut_partitions(long long nv, const long long *S, long long C, int *part_ptr, int *n_parts,
+                           cudaStream_t s, Arena &ar);
+cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci_out, long long total_nnz,
+                            int total_rows, cudaStream_t s, Arena &ar);
+
+}  // namespace sf

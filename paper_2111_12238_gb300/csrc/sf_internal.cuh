@@ -1,0 +1,109 @@
+// Internal declarations shared by the translation units of libsparsefusion.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sparsefusion.h"
+
+namespace sf {
+
+// Joint-DAG shapes built by the inspector (§2.2: the DAG of SpTRSV is the pattern of L,
+// SpMV has no intra-kernel edges, F carries the inter-kernel edges).
+//   K_SEP      vertices: kernel-1 rows 0..n-1 (tag 0), kernel-2 rows n..2n-1 (tag 1)
+//   K_PAIRED   one vertex per row holding both kernels' iteration i (F = I)
+//   K_PAIRED_T the reversed DAG of L (adjoint of SpTRSV->SpMV)
+//   K_SEP_T    reversed L solve (tag 0) then A^T rows (tag 1) (adjoint of SpMV->SpTRSV)
+enum Kind { K_SEP = 0, K_PAIRED = 1, K_PAIRED_T = 2, K_SEP_T = 3 };
+
+// Executor modes (which item kinds a launch runs).
+enum Mode {
+    M_TRSV_SPMV = 0,   // separated items: SpTRSV row (tag 0), SpMV row (tag 1)
+    M_SPMV_TRSV = 1,   // paired: r_i = b_i - A_i x_in, z_i = (r_i - L_i z) / L_ii
+    M_IC0_TRSV = 2,    // paired: up-looking IC0 row i, then solve row i
+    M_TRSV = 3,        // single kernel: SpTRSV row
+    M_IC0 = 4,         // single kernel: IC0 row
+    M_ADJ_TRSV_SPMV = 5,  // paired: u_j = (M^T gy)_j, lam_j = (u_j - (L^T lam)_j) / L_jj
+    M_ADJ_SPMV_TRSV = 6,  // separated: lam_j (tag 0), gx_j = -(A^T lam)_j (tag 1)
+    M_COUNT = 7
+};
+
+// Per-direction launch state, one 32-byte block in device memory. `epoch` numbers the
+// launches of the schedule: a ready flag equal to the current epoch means "published in
+// this launch", so flags never need clearing. The last warp to leave a launch resets
+// the ticket / done counters and advances the epoch (see k_exec).
+struct ExecState {
+    unsigned ticket;
+    unsigned done;
+    unsigned epoch;
+    unsigned abort;
+    unsigned err_code;
+    int err_row;
+    unsigned pad0, pad1;
+};
+
+// Argument block of the executor. Typed pointers are carried as void* and cast in the
+// kernel so that one host-side struct serves both element types.
+struct ExecArgs {
+    const int *order;
+    const int *part_ptr;
+    int n_parts;
+    int n;
+    int k;
+    int kt;                 // right-hand-side columns handled side by side (pow2 <= lanes)
+    unsigned *flags;
+    ExecState *st;
+    unsigned long long timeout_ns;
+    const int *Lrp, *Lci;               // L (lower, diagonal last)
+    const int *Mrp, *Mci;               // M or A
+    const int *LTrp, *LTci, *LTperm;    // L^T pattern and entry permutation into L
+    const int *MTrp, *MTci, *MTperm;    // M^T / A^T
+    const void *Lv, *Mv, *xin, *b, *gy, *saved;
+    void *y, *xs, *gb, *gx, *gL, *gM;
+};
+
+// launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
+cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a);
+cudaError_t launch_exec_pair(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a);
+cudaError_t launch_exec_adj(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a);
+int occupancy_fwd(int mode, int dtype, int lpr);
+int occupancy_pair(int mode, int dtype, int lpr);
+int occupancy_adj(int mode, int dtype, int lpr);
+cudaError_t launch_spmv(int dtype, int lpr, int kt, int nrows, int k, const int *rp, const int *ci,
+                        const void *v, const void *x, const void *b, void *y, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// PTX helpers: the memory-model operations the executor and inspector rely on.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void record_error(ExecState *st, unsigned code, int row) {
+    if (atomicCAS(&st->err_code, 0u, code) == 0u) st->err_row = row;
+}
+
+}  // namespace sf

@@ -1,0 +1,392 @@
+"""Python binding of libsparsefusion.so (ctypes): argument marshalling only.
+
+Every step of the inspector and the executor runs in the library's CUDA kernels; this
+module turns torch tensors into device pointers and streams, raises on error statuses,
+and wraps the fused pairs in ``torch.autograd.Function``s whose backward is the library's
+fused adjoint pass. There is no CPU fallback: if the library is missing or no CUDA device
+is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _build
+
+PAIRS = {"trsv_spmv": 0, "ic0_trsv": 1, "spmv_trsv": 2, "trsv": 3, "ic0": 4}
+SF_WANT_ADJOINT = 0x1
+STATUS = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_BAD_PATTERN", 3: "SF_ERR_CUDA", 4: "SF_ERR_OOM",
+          5: "SF_ERR_TIMEOUT", 6: "SF_ERR_BREAKDOWN", 7: "SF_ERR_NONFINITE", 8: "SF_ERR_UNSUPPORTED"}
+
+
+class SfCsr(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("n_cols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colidx", C.c_void_p)]
+
+
+class SfOptions(C.Structure):
+    _fields_ = [("part_cost_target", C.c_int64), ("lanes_per_row", C.c_int32), ("rhs_tile", C.c_int32),
+                ("g2_placement", C.c_int32), ("reserved", C.c_int32), ("timeout_ns", C.c_uint64),
+                ("flags", C.c_uint32), ("reserved2", C.c_uint32)]
+
+
+class SfInfo(C.Structure):
+    _fields_ = [("pair", C.c_int32), ("n", C.c_int32), ("k_hint", C.c_int32), ("instances", C.c_int32),
+                ("depth", C.c_int32), ("n_parts", C.c_int32), ("n_items", C.c_int64),
+                ("adj_depth", C.c_int32), ("adj_n_parts", C.c_int32), ("adj_n_items", C.c_int64),
+                ("lanes_per_row", C.c_int32), ("rhs_tile", C.c_int32),
+                ("part_cost_target", C.c_int64), ("adj_part_cost_target", C.c_int64),
+                ("packing", C.c_int32), ("reserved", C.c_int32),
+                ("reuse_ratio", C.c_double), ("inspect_ms", C.c_double)]
+
+
+class SparseFusionError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        super().__init__(f"{what}: {STATUS.get(status, status)}{(' - ' + detail) if detail else ''}")
+        self.status = status
+        self.detail = detail
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = C.c_void_p
+_SIGS = {
+    "sf_inspect": (C.c_int, [C.c_int, C.POINTER(SfCsr), C.POINTER(SfCsr), C.POINTER(SfOptions), _P, C.POINTER(_P)]),
+    "sf_inspect_batched": (C.c_int, [C.c_int, C.c_int32, C.POINTER(SfCsr), C.POINTER(SfCsr), C.POINTER(SfOptions),
+                                     _P, C.POINTER(_P)]),
+    "sf_execute": (C.c_int, [_P, C.c_int, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    "sf_adjoint": (C.c_int, [_P, C.c_int, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sf_spmv": (C.c_int, [C.c_int, C.c_int32, C.POINTER(SfCsr), _P, _P, _P, _P, _P]),
+    "sf_schedule_check": (C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
+    "sf_validate": (C.c_int, [_P]),
+    "sf_schedule_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "sf_schedule_query": (C.c_int, [_P, C.POINTER(SfInfo)]),
+    "sf_schedule_export": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "sf_schedule_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_set_timeout": (C.c_int, [_P, C.c_uint64]),
+    "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
+    "sf_schedule_destroy": (None, [_P]),
+    "sf_status_string": (C.c_char_p, [C.c_int]),
+    "sf_last_error_detail": (C.c_int, [C.c_char_p, C.c_size_t]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libsparsefusion.so (building it first when absent and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                if not build_if_missing:
+                    raise RuntimeError(f"{_build.LIB} is missing; build it with "
+                                       "`python -m paper_2111_12238_gb300._build`")
+                _build.build()
+            lib = C.CDLL(_build.LIB)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _detail() -> str:
+    buf = C.create_string_buffer(512)
+    load_library().sf_last_error_detail(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise SparseFusionError(st, what, _detail())
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _ptr(t: Optional[torch.Tensor], name: str = "tensor"):
+    if t is None:
+        return None
+    _require_cuda(t, name)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(dt: torch.dtype) -> int:
+    if dt == torch.float64:
+        return 0
+    if dt == torch.float32:
+        return 1
+    raise ValueError(f"unsupported dtype {dt}: float64 or float32")
+
+
+def _k_of(t: torch.Tensor) -> int:
+    return 1 if t.dim() == 1 else int(t.shape[1])
+
+
+@dataclass
+class DeviceCsr:
+    """A CSR pattern resident on the GPU (int32 rowptr / colidx)."""
+    n_rows: int
+    n_cols: int
+    rowptr: torch.Tensor
+    colidx: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    @classmethod
+    def from_host(cls, csr, device="cuda") -> "DeviceCsr":
+        rp = torch.from_numpy(np.ascontiguousarray(csr.rowptr, dtype=np.int32)).to(device)
+        ci = torch.from_numpy(np.ascontiguousarray(csr.colidx, dtype=np.int32)).to(device)
+        return cls(int(csr.n_rows), int(csr.n_cols), rp, ci)
+
+    def struct(self) -> SfCsr:
+        _require_cuda(self.rowptr, "rowptr")
+        _require_cuda(self.colidx, "colidx")
+        return SfCsr(self.n_rows, self.n_cols, self.nnz, self.rowptr.data_ptr(),
+                     self.colidx.data_ptr() if self.nnz else 0)
+
+
+def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns) -> SfOptions:
+    o = SfOptions()
+    o.part_cost_target = int(part_cost_target)
+    o.lanes_per_row = int(lanes_per_row)
+    o.rhs_tile = int(rhs_tile)
+    o.timeout_ns = int(timeout_ns)
+    o.flags = SF_WANT_ADJOINT if want_adjoint else 0
+    return o
+
+
+class Schedule:
+    """A fused schedule built by the GPU inspector; owns the library handle."""
+
+    def __init__(self, handle: C.c_void_p, pair: str, n: int, keep=()):
+        self._h = handle
+        self.pair = pair
+        self.n = n
+        self._keep = keep
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("schedule destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            load_library().sf_schedule_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- introspection
+    def info(self) -> dict:
+        inf = SfInfo()
+        _check(load_library().sf_schedule_query(self.handle, C.byref(inf)), "sf_schedule_query")
+        return {f: getattr(inf, f) for f, _ in SfInfo._fields_}
+
+    def export(self, which: int = 0) -> dict:
+        inf = self.info()
+        nv = inf["n_items"] if which == 0 else inf["adj_n_items"]
+        P = inf["n_parts"] if which == 0 else inf["adj_n_parts"]
+        level = np.zeros(nv, dtype=np.int32)
+        order = np.zeros(nv, dtype=np.int32)
+        pp = np.zeros(P + 1, dtype=np.int32)
+        _check(load_library().sf_schedule_export(self.handle, which, level.ctypes.data, order.ctypes.data,
+                                                 pp.ctypes.data), "sf_schedule_export")
+        depth = inf["depth"] if which == 0 else inf["adj_depth"]
+        return dict(level=level, order=order, part_ptr=pp, depth=depth)
+
+    def validate(self):
+        _check(load_library().sf_validate(self.handle), "sf_validate")
+
+    def check(self, stream=None):
+        """Synchronises and raises the first device-side failure recorded by executions."""
+        row = C.c_int32(-1)
+        st = load_library().sf_schedule_check(self.handle, _stream(stream), C.byref(row))
+        if st != 0:
+            raise SparseFusionError(st, "execution", _detail())
+
+    def check_status(self, stream=None):
+        row = C.c_int32(-1)
+        st = load_library().sf_schedule_check(self.handle, _stream(stream), C.byref(row))
+        return st, row.value
+
+    def set_launch(self, lanes_per_row=0, rhs_tile=0):
+        _check(load_library().sf_schedule_set_launch(self.handle, int(lanes_per_row), int(rhs_tile)),
+               "sf_schedule_set_launch")
+
+    def set_timeout(self, ns: int):
+        _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")
+
+    def debug_swap(self, q1: int, q2: int):
+        _check(load_library().sf_schedule_debug_swap(self.handle, int(q1), int(q2)), "sf_schedule_debug_swap")
+
+    # -- executor
+    def execute(self, L_vals, M_vals=None, b=None, x_in=None, y=None, x_save=None, stream=None):
+        """Runs the fused pair; returns y (allocated when not given)."""
+        ref = b if b is not None else L_vals
+        dt = _dtype_code(ref.dtype)
+        if self.pair == "ic0":
+            k = 1
+        else:
+            k = _k_of(b)
+            if y is None:
+                y = torch.empty_like(b)
+        st = load_library().sf_execute(self.handle, dt, k, _ptr(L_vals, "L_vals"), _ptr(M_vals, "M_vals"),
+                                       _ptr(x_in, "x_in"), _ptr(b, "b"), _ptr(y, "y"), _ptr(x_save, "x_save"),
+                                       _stream(stream))
+        _check(st, "sf_execute")
+        return y if self.pair != "ic0" else x_save
+
+    def adjoint(self, L_vals, M_vals, gy, saved=None, x_in=None, gb=None, gx=None, gL=None, gM=None, stream=None):
+        dt = _dtype_code(gy.dtype)
+        k = _k_of(gy)
+        if gb is None:
+            gb = torch.empty_like(gy)
+        st = load_library().sf_adjoint(self.handle, dt, k, _ptr(L_vals, "L_vals"), _ptr(M_vals, "M_vals"),
+                                       _ptr(x_in, "x_in"), _ptr(saved, "saved"), _ptr(gy, "gy"), _ptr(gb, "gb"),
+                                       _ptr(gx, "gx"), _ptr(gL, "gL"), _ptr(gM, "gM"), _stream(stream))
+        _check(st, "sf_adjoint")
+        return gb
+
+
+def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjoint=False, part_cost_target=0,
+            lanes_per_row=0, rhs_tile=0, timeout_ns=0, stream=None) -> Schedule:
+    lib = load_library()
+    o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns)
+    Ls = L.struct()
+    Ms = M.struct() if M is not None else None
+    h = C.c_void_p()
+    st = lib.sf_inspect(PAIRS[pair], C.byref(Ls), C.byref(Ms) if Ms is not None else None, C.byref(o),
+                        _stream(stream), C.byref(h))
+    _check(st, "sf_inspect")
+    return Schedule(h, pair, L.n_rows)
+
+
+def inspect_batched(pair: str, Ls: Sequence[DeviceCsr], Ms: Optional[Sequence[DeviceCsr]] = None, *,
+                    want_adjoint=False, part_cost_target=0, lanes_per_row=0, rhs_tile=0, timeout_ns=0,
+                    stream=None) -> Schedule:
+    lib = load_library()
+    o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns)
+    cnt = len(Ls)
+    la = (SfCsr * cnt)(*[x.struct() for x in Ls])
+    ma = (SfCsr * cnt)(*[x.struct() for x in Ms]) if Ms is not None else None
+    h = C.c_void_p()
+    st = lib.sf_inspect_batched(PAIRS[pair], cnt, la, ma, C.byref(o), _stream(stream), C.byref(h))
+    _check(st, "sf_inspect_batched")
+    return Schedule(h, pair, sum(x.n_rows for x in Ls))
+
+
+def spmv(M: DeviceCsr, vals: torch.Tensor, x: torch.Tensor, b: Optional[torch.Tensor] = None,
+         y: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """y = M x, or y = b - M x when b is given (the unfused SpMV launch)."""
+    lib = load_library()
+    k = _k_of(x)
+    if y is None:
+        y = torch.empty((M.n_rows,) + tuple(x.shape[1:]), dtype=x.dtype, device=x.device)
+    Ms = M.struct()
+    _check(lib.sf_spmv(_dtype_code(x.dtype), k, C.byref(Ms), _ptr(vals, "vals"), _ptr(x, "x"), _ptr(b, "b"),
+                       _ptr(y, "y"), _stream(stream)), "sf_spmv")
+    return y
+
+
+# ------------------------------------------------------------------------------ autograd
+class TrsvSpmv(torch.autograd.Function):
+    """y = M L^-1 b as one fused pass; backward is one fused adjoint pass."""
+
+    @staticmethod
+    def forward(ctx, sched: Schedule, L_vals, M_vals, b):
+        x = torch.empty_like(b)
+        y = sched.execute(L_vals, M_vals, b=b, x_save=x)
+        ctx.sched = sched
+        ctx.save_for_backward(L_vals, M_vals, x)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        L_vals, M_vals, x = ctx.saved_tensors
+        gy = gy.contiguous()
+        need_L, need_M = ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+        gL = torch.empty_like(L_vals) if need_L else None
+        gM = torch.empty_like(M_vals) if need_M else None
+        gb = ctx.sched.adjoint(L_vals, M_vals, gy, saved=x, gL=gL, gM=gM)
+        return None, gL, gM, gb
+
+
+class SpmvTrsv(torch.autograd.Function):
+    """z = L^-1 (b - A x_in) as one fused pass; backward is one fused adjoint pass."""
+
+    @staticmethod
+    def forward(ctx, sched: Schedule, L_vals, A_vals, x_in, b):
+        z = sched.execute(L_vals, A_vals, b=b, x_in=x_in)
+        ctx.sched = sched
+        ctx.save_for_backward(L_vals, A_vals, x_in, z)
+        return z
+
+    @staticmethod
+    def backward(ctx, gz):
+        L_vals, A_vals, x_in, z = ctx.saved_tensors
+        gz = gz.contiguous()
+        gL = torch.empty_like(L_vals) if ctx.needs_input_grad[1] else None
+        gA = torch.empty_like(A_vals) if ctx.needs_input_grad[2] else None
+        gx = torch.empty_like(x_in) if ctx.needs_input_grad[3] else None
+        gb = ctx.sched.adjoint(L_vals, A_vals, gz, saved=z, x_in=x_in, gx=gx, gL=gL, gM=gA)
+        return None, gL, gA, gx, gb
+
+
+def fused(sched: Schedule, *args):
+    """Differentiable fused pair: fused(sched, L_vals, M_vals, b) for 'trsv_spmv',
+    fused(sched, L_vals, A_vals, x_in, b) for 'spmv_trsv'."""
+    if sched.pair == "trsv_spmv":
+        return TrsvSpmv.apply(sched, *args)
+    if sched.pair == "spmv_trsv":
+        return SpmvTrsv.apply(sched, *args)
+    raise ValueError(f"no differentiable form for {sched.pair}")
+
+
+class GraphedExecute:
+    """One fused execution captured in a CUDA graph with static tensors: replay() re-runs
+    the persistent launch (the schedule's device-side epoch advances inside the graph)."""
+
+    def __init__(self, sched: Schedule, **static):
+        self.sched = sched
+        self.static = static
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            sched.execute(**static)          # first call allocates any library scratch
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.out = sched.execute(**static)
+
+    def replay(self):
+        self.graph.replay()
+        return self.out

@@ -1,0 +1,186 @@
+"""Fused executor parity with the FP64 oracle on small and ragged inputs: every pair,
+both element types, several right-hand-side counts and launch shapes, exact integer
+cases, and the unfused two-launch path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2111_12238_gb300 import inputs as I
+from paper_2111_12238_gb300 import sparsefusion as sf
+from tests._gpu import TOL, col_rel_err, dev_csr, host, need_cuda, t, vec_rel_err
+from tests._mats import dense_to_csr, random_lower
+
+pytestmark = pytest.mark.gpu
+
+
+def _lap3d(nx=14, k=1):
+    return I.trsv_spmv_lap3d_band(nx, per_row=6, halfband=200, seed=21, k=k)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("k", [1, 3, 16, 32, 40])
+@pytest.mark.parametrize("lpr", [0, 1, 4, 32])
+def test_trsv_spmv(dtype, k, lpr):
+    need_cuda()
+    w = _lap3d(11, k)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr)
+    xs = torch.empty((w.n, k), device="cuda", dtype=dtype)
+    y = sch.execute(t(w.L.vals, dtype), t(w.M.vals, dtype), b=t(w.b, dtype), x_save=xs)
+    sch.check()
+    assert col_rel_err(host(xs), x_ref) < TOL[dtype]
+    assert col_rel_err(host(y), y_ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("k", [1, 2, 16])
+@pytest.mark.parametrize("lpr", [0, 1, 8, 32])
+def test_spmv_trsv(dtype, k, lpr):
+    need_cuda()
+    w = I.spmv_trsv_powerlaw(n=20000, k=k, mean=16, lmax=400, halfband=900, seed=31)
+    z_ref = oracle.spmv_trsv(w.M, w.L, w.x_in, w.b)
+    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr)
+    z = sch.execute(t(w.L.vals, dtype), t(w.M.vals, dtype), b=t(w.b, dtype), x_in=t(w.x_in, dtype))
+    sch.check()
+    assert col_rel_err(host(z), z_ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("k", [1, 32])
+@pytest.mark.parametrize("lpr", [0, 4, 32])
+def test_ic0_trsv(dtype, k, lpr):
+    need_cuda()
+    w = I.ic0_trsv_aniso3d(12, k=k)
+    lf_ref, y_ref = oracle.ic0_trsv(w.L, w.b)
+    sch = sf.inspect("ic0_trsv", dev_csr(w.L), lanes_per_row=lpr)
+    lf = torch.empty(w.L.nnz, device="cuda", dtype=dtype)
+    y = sch.execute(t(w.L.vals, dtype), b=t(w.b, dtype), x_save=lf)
+    sch.check()
+    assert vec_rel_err(host(lf), lf_ref) < TOL[dtype]
+    assert col_rel_err(host(y), y_ref) < TOL[dtype] * (10 if dtype == torch.float32 else 1)
+
+
+def test_ic0_with_intersections_and_alone():
+    need_cuda()
+    nx = 30
+    offs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    n, rowptr, cols, soffs, Msk = I._stencil_pattern((nx, nx), offs)
+    vals = np.where(np.asarray([o == (0, 0) for o in soffs])[None, :], 9.0, -1.0)
+    A = I._finish(n, n, rowptr, cols, np.broadcast_to(vals, Msk.shape)[Msk])
+    L = I.lower_part(A)
+    lf_ref = oracle.ic0(L)
+    for lpr in (1, 4, 32):
+        sch = sf.inspect("ic0", dev_csr(L), lanes_per_row=lpr)
+        lf = torch.empty(L.nnz, device="cuda", dtype=torch.float64)
+        sch.execute(t(L.vals), x_save=lf)
+        sch.check()
+        assert vec_rel_err(host(lf), lf_ref) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_trsv_alone_and_unfused_path(k):
+    need_cuda()
+    w = _lap3d(10, k)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    st = sf.inspect("trsv", dev_csr(w.L))
+    x = st.execute(t(w.L.vals), b=t(w.b))
+    y = sf.spmv(dev_csr(w.M), t(w.M.vals), x)
+    st.check()
+    assert col_rel_err(host(x), x_ref) < 1e-12
+    assert col_rel_err(host(y), y_ref) < 1e-12
+    r = sf.spmv(dev_csr(w.M), t(w.M.vals), t(w.b), b=t(w.b))
+    torch.cuda.synchronize()
+    assert col_rel_err(host(r), oracle.residual(w.M, w.b, w.b)) < 1e-12
+
+
+def test_integer_exact_bitwise():
+    # unit lower-triangular {-1,0,1} L, integer M and b: every partial sum is an exact
+    # integer, so the fused result must equal the oracle bit for bit in any summation order
+    need_cuda()
+    n = 3000
+    rng_pat = I.powerlaw_lower(n, 3, 12, 77)
+    Lv = np.where(rng_pat.colidx == np.repeat(np.arange(n), np.diff(rng_pat.rowptr)), 1.0,
+                  np.sign(rng_pat.vals)).astype(np.float64)
+    L = I.Csr(n, n, rng_pat.rowptr, rng_pat.colidx, Lv)
+    # keep the solution bounded: b = L * x_int with small integer x_int
+    x_int = (np.arange(n) % 5 - 2).astype(np.float64).reshape(n, 1)
+    b = oracle.spmv(L, x_int)
+    Mp = I.band_random(n, 4, 20, 5)
+    M = I.Csr(n, n, Mp.rowptr, Mp.colidx, np.round(Mp.vals * 4))
+    x_ref, y_ref = oracle.trsv_spmv(L, M, b)
+    assert np.array_equal(x_ref, x_int)
+    for lpr in (1, 4, 32):
+        sch = sf.inspect("trsv_spmv", dev_csr(L), dev_csr(M), lanes_per_row=lpr)
+        xs = torch.empty((n, 1), device="cuda", dtype=torch.float64)
+        y = sch.execute(t(L.vals), t(M.vals), b=t(b), x_save=xs)
+        sch.check()
+        assert np.array_equal(host(xs), x_ref)
+        assert np.array_equal(host(y), y_ref)
+
+
+def test_edge_cases_tiny_and_diagonal():
+    need_cuda()
+    # n = 1
+    L1 = dense_to_csr(np.array([[4.0]]))
+    M1 = dense_to_csr(np.array([[-2.0]]))
+    b1 = np.array([[3.0]])
+    sch = sf.inspect("trsv_spmv", dev_csr(L1), dev_csr(M1))
+    y = sch.execute(t(L1.vals), t(M1.vals), b=t(b1))
+    sch.check()
+    assert host(y)[0, 0] == -2.0 * (3.0 / 4.0)
+    # diagonal L (depth 1) and an M with empty rows
+    n = 1000
+    d = 1.0 + np.arange(n) % 7
+    L = dense_to_csr(np.diag(d))
+    D = np.zeros((n, n))
+    D[::3, 5] = 1.5
+    M = dense_to_csr(D)
+    b = I.dense_vectors(n, 2, 3, I.S_RHS)
+    x_ref, y_ref = oracle.trsv_spmv(L, M, b)
+    sch = sf.inspect("trsv_spmv", dev_csr(L), dev_csr(M))
+    assert sch.info()["depth"] == 2
+    y = sch.execute(t(L.vals), t(M.vals), b=t(b))
+    sch.check()
+    assert col_rel_err(host(y), y_ref) < 1e-15
+    # dense lower triangle (long rows, depth n)
+    Dd = random_lower(200, 1.0, 5)
+    Ld = dense_to_csr(Dd)
+    bd = I.dense_vectors(200, 1, 2, I.S_RHS)
+    for lpr in (1, 32):
+        sch = sf.inspect("trsv", dev_csr(Ld), lanes_per_row=lpr)
+        x = sch.execute(t(Ld.vals), b=t(bd))
+        sch.check()
+        assert col_rel_err(host(x), oracle.trsv_lower(Ld, bd)) < 1e-12
+
+
+def test_repeated_launches_and_epochs():
+    # many launches of one schedule: flags are never cleared, the epoch advances
+    need_cuda()
+    w = _lap3d(9, 1)
+    _, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M))
+    Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
+    y = torch.empty_like(b)
+    for _ in range(50):
+        sch.execute(Lv, Mv, b=b, y=y)
+    sch.check()
+    assert col_rel_err(host(y), y_ref) < 1e-12
+    # changing k between launches reuses the same schedule
+    b3 = t(np.repeat(w.b, 3, axis=1))
+    y3 = sch.execute(Lv, Mv, b=b3)
+    sch.check()
+    assert col_rel_err(host(y3), np.repeat(y_ref, 3, axis=1)) < 1e-12
+
+
+def test_cuda_graph_replay():
+    need_cuda()
+    w = _lap3d(10, 1)
+    _, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M))
+    g = sf.GraphedExecute(sch, L_vals=t(w.L.vals), M_vals=t(w.M.vals), b=t(w.b), y=torch.empty((w.n, 1), device="cuda",
+                                                                                             dtype=torch.float64))
+    for _ in range(5):
+        out = g.replay()
+    sch.check()
+    assert col_rel_err(host(out), y_ref) < 1e-12

@@ -1,0 +1,557 @@
+"""Benchmark of the fused sparse-fusion hot path on synthetic workloads.
+
+Default workload (N=1): SpTRSV then SpMV on the 128^3 grid (L = lower 7-point pattern,
+n = 2,097,152; M = 8 entries per row in a +-1000 band), FP64, one right-hand side; one step
+is one fused forward pass (y = M L^-1 b, x saved) plus one fused adjoint pass (gb, gL, gM).
+Other workloads: --workload lap2d64 | aniso100 | batched512 | powerlaw4m.
+
+Prints one JSON line (rank 0). `value` is solves per second of the whole job with inputs
+resident in HBM; `e2e` repeats the measurement through the same public calls with the
+right-hand sides copied in from pinned host memory and the results copied back every step.
+`--impl reference` times the sequential FP64 CPU oracle on the same workload instead.
+For N > 1 (torchrun) every rank runs an independent replica of the workload (a single
+triangular system does not shard); the value is the sum over ranks over the slowest rank's
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused-pair solves/s, HBM GB/s (% peak) vs unfused same GPU; adjoint/fwd ratio"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _csrc_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2111_12238_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(workload, kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("csrc_hash") != _csrc_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- workloads
+def csr_bytes(nnz, n, es):
+    return (es + 4) * nnz + 4 * (n + 1)
+
+
+def make_workload(name, dtype_name):
+    from paper_2111_12238_gb300 import inputs as I
+    es = 8 if dtype_name == "f64" else 4
+    if name == "lap2d64":
+        w = I.trsv_spmv_lap2d(64, seed=1)
+        adj = False
+    elif name == "lap3d128":
+        w = I.trsv_spmv_lap3d_band(128, seed=2)
+        adj = True
+    elif name == "aniso100":
+        w = I.ic0_trsv_aniso3d(100, k=32, seed=3)
+        adj = False
+    elif name == "batched512":
+        w = I.batched_trsv_spmv(512, seed=4)
+        adj = True
+    elif name == "powerlaw4m":
+        w = I.spmv_trsv_powerlaw(seed=5)
+        adj = True
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    n, k = w.n, w.k
+    if w.instances:
+        nnzL = sum(x.L.nnz for x in w.instances)
+        nnzM = sum(x.M.nnz for x in w.instances)
+    else:
+        nnzL = w.L.nnz
+        nnzM = w.M.nnz if w.M is not None else 0
+    vec = es * n * k
+    if w.pair == "trsv_spmv":
+        fwd_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec      # b in, x and y out
+        adj_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec + es * (nnzL + nnzM)
+        fwd_flops = 2 * (nnzL + nnzM) * k
+    elif w.pair == "spmv_trsv":
+        fwd_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec      # x_in, b in, z out
+        adj_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 5 * vec + es * (nnzL + nnzM)
+        fwd_flops = 2 * (nnzL + nnzM) * k
+    else:  # ic0_trsv: read tril(A) values + pattern, write factor values, b in, y out
+        fwd_bytes = csr_bytes(nnzL, n, es) + es * nnzL + 2 * vec
+        adj_bytes = 0
+        fwd_flops = 2 * nnzL * k + 4 * nnzL
+    return dict(w=w, name=name, pair=w.pair, n=n, k=k, nnzL=nnzL, nnzM=nnzM, adj=adj, es=es,
+                fwd_bytes=fwd_bytes, adj_bytes=adj_bytes, fwd_flops=fwd_flops,
+                fits_l2=(fwd_bytes < 129e6))
+
+
+def _concat_vals(w, which):
+    if w.instances:
+        return np.concatenate([getattr(x, which).vals for x in w.instances])
+    return getattr(w, which).vals
+
+
+class Gpu:
+    """Device state of one workload: schedule, resident inputs, outputs, unfused path."""
+
+    def __init__(self, wl, dtype_name, device, launch_opts=None):
+        import torch
+        launch_opts = launch_opts or {}
+        from paper_2111_12238_gb300 import sparsefusion as sf
+        self.torch, self.sf, self.wl = torch, sf, wl
+        w = wl["w"]
+        dt = torch.float64 if dtype_name == "f64" else torch.float32
+        self.dt = dt
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        pair = w.pair
+        self.pair = pair
+        if w.instances:
+            Ls = [sf.DeviceCsr.from_host(x.L, device) for x in w.instances]
+            Ms = [sf.DeviceCsr.from_host(x.M, device) for x in w.instances]
+            t0 = time.perf_counter()
+            self.sched = sf.inspect_batched(pair, Ls, Ms, want_adjoint=wl["adj"], **launch_opts)
+            torch.cuda.synchronize()
+            self.inspect_s = time.perf_counter() - t0
+            self.un_sched = sf.inspect_batched("trsv", Ls, **launch_opts)
+            # unfused SpMV over the block-diagonal M: concatenate the patterns on the host
+            from paper_2111_12238_gb300 import inputs as I
+            rp, ci, off, offn = [0], [], 0, 0
+            for x in w.instances:
+                rp.extend((x.M.rowptr[1:].astype(np.int64) + off).tolist())
+                ci.append(x.M.colidx.astype(np.int64) + offn)
+                off += x.M.nnz
+                offn += x.n
+            Mcat = I.Csr(w.n, w.n, np.asarray(rp, dtype=np.int32), np.concatenate(ci).astype(np.int32),
+                         np.zeros(off))
+            self.M_dev = sf.DeviceCsr.from_host(Mcat, device)
+        else:
+            self.L_dev = sf.DeviceCsr.from_host(w.L, device)
+            self.M_dev = sf.DeviceCsr.from_host(w.M, device) if w.M is not None else None
+            t0 = time.perf_counter()
+            self.sched = sf.inspect(pair, self.L_dev, self.M_dev, want_adjoint=wl["adj"], **launch_opts)
+            torch.cuda.synchronize()
+            self.inspect_s = time.perf_counter() - t0
+            self.un_sched = sf.inspect("ic0" if pair == "ic0_trsv" else "trsv", self.L_dev, **launch_opts)
+            self.un_sched2 = sf.inspect("trsv", self.L_dev, **launch_opts) if pair == "ic0_trsv" else None
+        self.Lv = T(_concat_vals(w, "L"))
+        self.Mv = T(_concat_vals(w, "M")) if w.M is not None else None
+        self.b = T(w.b)
+        self.x_in = T(w.x_in) if w.x_in is not None else None
+        self.gy = T(w.gy) if w.gy is not None else None
+        self.y = torch.empty_like(self.b)
+        self.xs = (torch.empty_like(self.b) if pair == "trsv_spmv"
+                   else torch.empty(self.Lv.numel(), device=device, dtype=dt) if pair == "ic0_trsv" else None)
+        if wl["adj"]:
+            self.gb = torch.empty_like(self.b)
+            self.gL = torch.empty_like(self.Lv)
+            self.gM = torch.empty_like(self.Mv)
+            self.gx = torch.empty_like(self.x_in) if self.x_in is not None else None
+        self.tmp = torch.empty_like(self.b)
+        self.tmp2 = torch.empty_like(self.b)
+        self.stream = torch.cuda.current_stream()
+
+    def fwd(self):
+        self.sched.execute(self.Lv, self.Mv, b=self.b, x_in=self.x_in, y=self.y, x_save=self.xs)
+
+    def adj(self):
+        s = self.sched
+        if self.pair == "trsv_spmv":
+            s.adjoint(self.Lv, self.Mv, self.gy, saved=self.xs, gb=self.gb, gL=self.gL, gM=self.gM)
+        else:
+            s.adjoint(self.Lv, self.Mv, self.gy, saved=self.y, x_in=self.x_in, gb=self.gb, gx=self.gx,
+                      gL=self.gL, gM=self.gM)
+
+    def unfused(self):
+        sf = self.sf
+        if self.pair == "trsv_spmv":
+            self.un_sched.execute(self.Lv, b=self.b, y=self.tmp)
+            sf.spmv(self.M_dev, self.Mv, self.tmp, y=self.tmp2)
+        elif self.pair == "spmv_trsv":
+            sf.spmv(self.M_dev, self.Mv, self.x_in, b=self.b, y=self.tmp)
+            self.un_sched.execute(self.Lv, b=self.tmp, y=self.tmp2)
+        else:
+            self.un_sched.execute(self.Lv, x_save=self.xs)
+            self.un_sched2.execute(self.xs, b=self.b, y=self.tmp2)
+
+    def check(self):
+        self.sched.check()
+        self.un_sched.check()
+
+
+def _time_loop(torch, fns, steps, flush=None):
+    """Runs `steps` iterations of the launches in `fns` on the current stream with CUDA
+    events around each launch; returns (total_ms, [per-fn total ms])."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        if flush is not None:
+            flush()
+        ev[s][0].record()
+        for i, f in enumerate(fns):
+            f()
+            ev[s][i + 1].record()
+    torch.cuda.synchronize()
+    per = [0.0] * len(fns)
+    total = 0.0
+    for s in range(steps):
+        for i in range(len(fns)):
+            dtm = ev[s][i].elapsed_time(ev[s][i + 1])
+            per[i] += dtm
+            total += dtm
+    return total, per
+
+
+def _gpu_id(torch, local):
+    """nvidia-smi id of this process's GPU (its UUID), falling back to the ordinal."""
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons, loaded = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                s_, m_ = float(r[1]), float(r[2])
+            except (ValueError, IndexError):
+                continue
+            sm.append(s_)
+            mx.append(m_)
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def t_hop_ns(torch, device):
+    """Latency of one dependence hop: a bidiagonal chain solved through the executor with
+    one row per partition (every row waits for the previous one, drawn by another warp),
+    time / rows."""
+    from paper_2111_12238_gb300 import inputs as I
+    from paper_2111_12238_gb300 import sparsefusion as sf
+    n = 100000
+    rp = np.concatenate([[0], np.arange(1, 2 * n, 2)]).astype(np.int32)
+    ci = np.empty(2 * n - 1, dtype=np.int32)
+    ci[0] = 0
+    ci[1::2] = np.arange(0, n - 1)
+    ci[2::2] = np.arange(1, n)
+    vals = np.where(np.arange(2 * n - 1) % 2 == 0, 2.0, 0.5)
+    L = I.Csr(n, n, rp, ci, vals)
+    s = sf.inspect("trsv", sf.DeviceCsr.from_host(L, device), lanes_per_row=1, part_cost_target=1)
+    Lv = torch.from_numpy(vals).to(device)
+    b = torch.ones((n, 1), device=device, dtype=torch.float64)
+    y = torch.empty_like(b)
+    for _ in range(2):
+        s.execute(Lv, b=b, y=y)
+    ms, _ = _time_loop(torch, [lambda: s.execute(Lv, b=b, y=y)], 3)
+    s.check()
+    return ms / 3 * 1e6 / n
+
+
+# ----------------------------------------------------------------------------- arms
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(device))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_12238_gb300 import sparsefusion as sf  # noqa: F401
+
+    wl = make_workload(args.workload, args.dtype)
+    launch_opts = dict(lanes_per_row=args.lanes, blocks_per_sm=args.blocks_per_sm, epoch_flags=args.epoch_flags,
+                       part_cost_target=args.part_cost, dynamic_queue=args.dynamic_queue)
+    g = Gpu(wl, args.dtype, device, launch_opts)
+    fns = [g.fwd] + ([g.adj] if wl["adj"] else [])
+    flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device) if wl["fits_l2"] else None
+    flush = (lambda: flush_buf.zero_()) if flush_buf is not None else None
+    for _ in range(args.warmup):
+        for f in fns:
+            f()
+        g.unfused()
+    g.check()
+    if args.steps is None:
+        # size the timed region to about 3 s of device time
+        one, _ = _time_loop(torch, fns, 3, flush)
+        args.steps = int(min(2000, max(20, 3000.0 / max(one / 3, 1e-3))))
+
+    # ---- timed region (device-resident inputs)
+    clk = ClockSampler(_gpu_id(torch, local))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total_ms, per = _time_loop(torch, fns, args.steps, flush)
+    clocks = clk.stop()
+    g.check()
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    fwd_ms = per[0] / args.steps
+    adj_ms = per[1] / args.steps if wl["adj"] else None
+
+    # ---- unfused two-launch path on the same GPU
+    un_ms, _ = _time_loop(torch, [g.unfused], max(10, args.steps // 4), flush)
+    un_ms /= max(10, args.steps // 4)
+    g.check()
+
+    # ---- end to end through the public calls with host buffers
+    pin_b = g.b.cpu().pin_memory()
+    pin_gy = g.gy.cpu().pin_memory() if wl["adj"] else None
+    out_y = torch.empty(g.y.shape, dtype=g.dt, pin_memory=True)
+    out_gb = torch.empty(g.y.shape, dtype=g.dt, pin_memory=True) if wl["adj"] else None
+
+    def e2e_step():
+        g.b.copy_(pin_b, non_blocking=True)
+        if pin_gy is not None:
+            g.gy.copy_(pin_gy, non_blocking=True)
+        g.fwd()
+        if wl["adj"]:
+            g.adj()
+            out_gb.copy_(g.gb, non_blocking=True)
+        out_y.copy_(g.y, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_steps = max(5, args.steps // 10)
+    for _ in range(2):
+        e2e_step()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    g.check()
+    h2d = pin_b.numel() * pin_b.element_size() + (pin_gy.numel() * pin_gy.element_size() if pin_gy is not None else 0)
+    d2h = out_y.numel() * out_y.element_size() + (out_gb.numel() * out_gb.element_size() if out_gb is not None else 0)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    hbm, peak_src = _peaks()
+    info = g.sched.info()
+    dom = "fwd" if (adj_ms is None or fwd_ms >= adj_ms) else "adj"
+    dom_ms = fwd_ms if dom == "fwd" else adj_ms
+    dom_bytes = wl["fwd_bytes"] if dom == "fwd" else wl["adj_bytes"]
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = _recorded_traffic(args.workload, dom)
+    thop = t_hop_ns(torch, device)
+    depth = info["depth"] if dom == "fwd" else info["adj_depth"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": args.dtype,
+        "data": "synthetic",
+        "config": {
+            "workload": wl["w"].name,
+            "pair": wl["pair"],
+            "n": wl["n"], "k": wl["k"], "nnz_L": wl["nnzL"], "nnz_M": wl["nnzM"],
+            "step": "one fused forward pass" + (" + one fused adjoint pass" if wl["adj"] else ""),
+            "l2": "L2 flushed (256 MB write) between steps" if wl["fits_l2"] else
+                  "inputs larger than L2, no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "instances": len(wl["w"].instances) or 1,
+        },
+        "roofline": {
+            "kernel": f"k_exec ({dom})",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": hbm,
+            "unit": "GB/s",
+            "frac": achieved / hbm,
+            "traffic": traffic,
+            "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": dom_bytes,
+            "latency_bound_ms": depth * thop * 1e-6,
+            "hbm_bound_ms": dom_bytes / (hbm * 1e9) * 1e3,
+        },
+        "fwd_ms": fwd_ms,
+        "adj_ms": adj_ms,
+        "adjoint_fwd_ratio": (adj_ms / fwd_ms) if adj_ms else None,
+        "fwd_solves_per_s": 1e3 / fwd_ms,
+        "fwd_gbs": wl["fwd_bytes"] / (fwd_ms / 1e3) / 1e9,
+        "adj_gbs": (wl["adj_bytes"] / (adj_ms / 1e3) / 1e9) if adj_ms else None,
+        "unfused_fwd_ms": un_ms,
+        "fused_speedup_vs_unfused": un_ms / fwd_ms,
+        "depth": info["depth"], "adj_depth": info["adj_depth"],
+        "t_hop_ns": thop,
+        "inspect_ms": g.inspect_s * 1e3,
+        "ner_vs_unfused": (g.inspect_s * 1e3 / (un_ms - fwd_ms)) if un_ms > fwd_ms else None,
+        "lanes_per_row": info["lanes_per_row"], "n_parts": info["n_parts"],
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": len(fns) * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_step(wl):
+    import oracle
+    w = wl["w"]
+    items = w.instances if w.instances else [w]
+
+    def step():
+        for x in items:
+            if x.pair == "trsv_spmv":
+                xx, _ = oracle.trsv_spmv(x.L, x.M, x.b)
+                if wl["adj"]:
+                    oracle.adj_trsv_spmv(x.L, x.M, xx, x.gy)
+            elif x.pair == "spmv_trsv":
+                z = oracle.spmv_trsv(x.M, x.L, x.x_in, x.b)
+                if wl["adj"]:
+                    oracle.adj_spmv_trsv(x.M, x.L, x.x_in, z, x.gy)
+            else:
+                oracle.ic0_trsv(x.L, x.b)
+    return step, len(items)
+
+
+def cpu_baseline(wl, seconds):
+    """The sequential FP64 oracle (one host core) on the same workload, repeated for about
+    `seconds` of CPU time."""
+    step, _ = _oracle_step(wl)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        step()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": reps / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full steps of the workload ({el:.1f} s), single-threaded C, "
+                      f"host has {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, "f64")
+    step, _ = _oracle_step(wl)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["w"].name, "pair": wl["pair"], "n": wl["n"], "k": wl["k"],
+                       "step": "oracle forward" + (" + adjoint" if wl["adj"] else "")},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full steps, single-threaded C"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--workload", default="lap3d128",
+                    choices=["lap2d64", "lap3d128", "aniso100", "batched512", "powerlaw4m"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per row (0 = auto)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="executor blocks per SM (0 = occupancy)")
+    ap.add_argument("--part-cost", type=int, default=0, help="partition cost target (0 = auto)")
+    ap.add_argument("--epoch-flags", action="store_true", help="publish through epoch flags even for k = 1")
+    ap.add_argument("--dynamic-queue", action="store_true", help="draw partitions from a ticket counter")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.steps = args.steps if args.steps is not None else 20
+        args.warmup = args.warmup if args.warmup is not None else 3
+        run_reference(args)
+        return
+    args.warmup = max(3, args.warmup if args.warmup is not None else 20)
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

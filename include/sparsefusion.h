@@ -73,14 +73,20 @@ typedef struct {
 
 /* Options; a zero-initialised struct selects every default. */
 #define SF_WANT_ADJOINT 0x1u /* also build the transposed schedule used by sf_adjoint */
+#define SF_EPOCH_FLAGS 0x2u  /* publish rows through per-row epoch flags even when k = 1
+                                (by default a single right-hand side is published by its value:
+                                the dependency vector is reset to an all-ones NaN pattern
+                                before each launch and a consumer waits for its entry to change) */
+#define SF_DYNAMIC_QUEUE 0x4u /* warps draw partitions from a ticket counter instead of the
+                                default static round robin over a cooperative launch */
 typedef struct {
     int64_t part_cost_target; /* C of the partition cut (§3.1 vertex cost); 0 = auto  */
     int32_t lanes_per_row;    /* lanes of a warp working on one row: 1..32 (pow2); 0 = auto */
     int32_t rhs_tile;         /* right-hand-side columns handled side by side; 0 = auto */
     int32_t g2_placement;     /* reserved, must be 0 (as-soon-as-possible placement) */
-    int32_t reserved;         /* must be 0 */
+    int32_t blocks_per_sm;    /* resident executor blocks per SM; 0 = occupancy limit  */
     uint64_t timeout_ns;      /* limit of one dependence wait on the GPU; 0 = 2 s    */
-    uint32_t flags;           /* SF_WANT_ADJOINT                                      */
+    uint32_t flags;           /* SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE  */
     uint32_t reserved2;       /* must be 0 */
 } sf_options;
 
@@ -121,7 +127,11 @@ sf_status sf_inspect_batched(sf_pair pair, int32_t count, const sf_csr *Ls, cons
  *          (required for SF_IC0). When NULL a library-owned buffer is used; it is
  *          allocated on the first call that needs it, so make one such call before
  *          capturing the stream into a CUDA graph.
- *  k:      number of right-hand sides, 1 <= k <= 1024.
+ *  k:      number of right-hand sides, 1 <= k <= 1024. With k = 1 (unless SF_EPOCH_FLAGS
+ *          was given) the vector that carries the dependences (x_save or its library-owned
+ *          stand-in for SF_TRSV_SPMV, y for SF_TRSV and SF_SPMV_TRSV) is first filled with
+ *          the all-ones pattern on `stream`; a result whose bits equal that pattern is
+ *          stored as the canonical NaN instead (both are NaN).
  * Concurrent calls with the same schedule on different streams race; calls on one
  * stream are ordered. Returns after enqueueing the launch. */
 sf_status sf_execute(const sf_schedule *sch, sf_dtype dt, int32_t k, const void *L_vals,
@@ -175,7 +185,9 @@ typedef struct {
     int32_t lanes_per_row, rhs_tile;
     int64_t part_cost_target, adj_part_cost_target;
     int32_t packing;                   /* 0 separated, 1 interleaved (paired rows) */
-    int32_t reserved;
+    int32_t blocks_per_sm;             /* 0 = occupancy limit */
+    int32_t epoch_flags;               /* 1 when SF_EPOCH_FLAGS is in effect */
+    int32_t dynamic_queue;             /* 1 when SF_DYNAMIC_QUEUE is in effect */
     double reuse_ratio;                /* Table 2 / §2.2 reuse ratio of the pair */
     double inspect_ms;                 /* wall time of the inspector call */
 } sf_info;
@@ -188,9 +200,12 @@ sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 sf_status sf_schedule_export(const sf_schedule *sch, int32_t which, int32_t *level,
                              int32_t *order, int32_t *part_ptr);
 
-/* Changes launch parameters without re-inspecting: lanes_per_row (1..32, pow2) and
- * rhs_tile (1..lanes_per_row, pow2); 0 keeps the current value. */
-sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_t rhs_tile);
+/* Changes launch parameters without re-inspecting: lanes_per_row (1..32, pow2), rhs_tile
+ * (1..lanes_per_row, pow2) and blocks_per_sm (>= 1); 0 keeps the current value.
+ * epoch_flags: 1 always publishes through epoch flags, 0 uses value flags when k = 1,
+ * -1 keeps the current setting. */
+sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_t rhs_tile,
+                                 int32_t blocks_per_sm, int32_t epoch_flags);
 
 /* Sets the time limit of one dependence wait (0 = 2 s). */
 sf_status sf_schedule_set_timeout(sf_schedule *sch, uint64_t timeout_ns);

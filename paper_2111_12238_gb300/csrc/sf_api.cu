@@ -97,6 +97,9 @@ struct sf_schedule {
     bool hasLT = false, hasMT = false;
     Dir fwd, adj;
     int lpr = 4, kt = 0;
+    int blocks_per_sm = 0;
+    bool epoch_flags = false;
+    bool dynamic_queue = false;
     unsigned long long timeout_ns = 2000000000ull;
     double reuse = 0.0, inspect_ms = 0.0;
     int packing = 0;
@@ -116,9 +119,11 @@ sf_status validate_options(const sf_options *o) {
         return fail(SF_ERR_INVALID_ARG, "lanes_per_row must be 0 or a power of two in [1, 32]");
     if (o->rhs_tile != 0 && !is_pow2_upto32(o->rhs_tile))
         return fail(SF_ERR_INVALID_ARG, "rhs_tile must be 0 or a power of two in [1, 32]");
-    if (o->g2_placement != 0 || o->reserved != 0 || o->reserved2 != 0)
+    if (o->g2_placement != 0 || o->reserved2 != 0)
         return fail(SF_ERR_INVALID_ARG, "g2_placement and reserved fields must be 0");
-    if (o->flags & ~SF_WANT_ADJOINT) return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
+    if (o->blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
+    if (o->flags & ~(SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE))
+        return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
     return SF_OK;
 }
 
@@ -199,8 +204,10 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     if (e != cudaSuccess) return from_cuda(e, "cost prefix");
     long long C = C_user;
     if (C <= 0) {
+        // a partition of about max(1, G/4) items, G = 32 / lanes the groups of a warp: small
+        // enough that a late item delays few others, large enough to keep groups busy
         const long long mean = std::max<long long>(1, (total + nv - 1) / nv);
-        C = (long long)(32 / S->lpr) * 2 * mean;
+        C = (long long)std::max(1, (32 / S->lpr) / 4) * mean;
     }
     d.C = C;
     e = cut_partitions(nv, Sx, C, d.part_ptr, &d.n_parts, s, tmp);
@@ -227,14 +234,15 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
         SF_CK(transpose_csr(S->M, S->MT, s, tmp, S->keep), "transpose of M");
         S->hasMT = true;
     }
-    // launch shape: lanes per row from the mean number of nonzeros per joint-DAG vertex
+    // launch shape: one lane per row while rows are short (each lane then keeps several
+    // rows in flight); wider groups for long rows, and at least the right-hand-side tile
     if (o.lanes_per_row) {
         S->lpr = o.lanes_per_row;
     } else {
         const long long nnz = S->L.nnz + (S->hasM ? S->M.nnz : 0);
         const long long nv = (S->pair == SF_TRSV_SPMV) ? 2LL * S->n : S->n;
         const long long mean = std::max<long long>(1, (nnz + nv - 1) / nv);
-        S->lpr = std::min(32, pow2_ceil((mean + 1) / 2));
+        S->lpr = std::min(32, pow2_ceil((mean + 31) / 32));
     }
     S->kt = o.rhs_tile;
     if (S->kt > S->lpr) S->lpr = S->kt;
@@ -269,6 +277,9 @@ sf_status finish_inspect(sf_schedule *S, const sf_options &o, cudaStream_t s, sf
         return st;
     }
     if (o.timeout_ns) S->timeout_ns = o.timeout_ns;
+    S->blocks_per_sm = o.blocks_per_sm;
+    S->epoch_flags = (o.flags & SF_EPOCH_FLAGS) != 0;
+    S->dynamic_queue = (o.flags & SF_DYNAMIC_QUEUE) != 0;
     S->inspect_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = S;
     return SF_OK;
@@ -307,19 +318,31 @@ sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void 
     return SF_OK;
 }
 
-int occupancy(int mode, int dtype, int lpr) {
+int occupancy(int mode, int dtype, int lpr, bool vf) {
     static std::mutex mu;
-    static int cache[M_COUNT][2][6] = {};
+    static int cache[M_COUNT][2][6][2] = {};
     int li = 0;
     while ((1 << li) < lpr) ++li;
     std::lock_guard<std::mutex> lk(mu);
-    int &c = cache[mode][dtype][li];
+    int &c = cache[mode][dtype][li][vf ? 1 : 0];
     if (!c) {
-        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr);
-        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) c = occupancy_adj(mode, dtype, lpr);
-        else c = occupancy_pair(mode, dtype, lpr);
+        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf);
+        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) c = occupancy_adj(mode, dtype, lpr, vf);
+        else c = occupancy_pair(mode, dtype, lpr, vf);
     }
     return c;
+}
+
+// Buffer through which a value-flag launch publishes its rows (k = 1), or NULL.
+void *value_flag_buffer(int mode, const ExecArgs &a) {
+    switch (mode) {
+        case M_TRSV_SPMV: return a.xs;
+        case M_TRSV:
+        case M_SPMV_TRSV: return a.y;
+        case M_ADJ_TRSV_SPMV:
+        case M_ADJ_SPMV_TRSV: return a.gb;
+        default: return nullptr;
+    }
 }
 
 sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int k, ExecArgs &a, cudaStream_t s) {
@@ -331,6 +354,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     a.n = S->n;
     a.k = k;
     a.kt = kt;
+    a.dynamic = S->dynamic_queue ? 1 : 0;
     a.flags = d.flags;
     a.st = d.st;
     a.timeout_ns = S->timeout_ns;
@@ -345,14 +369,19 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     a.MTci = S->hasMT ? S->MT.t.colidx : nullptr;
     a.MTperm = S->hasMT ? S->MT.perm : nullptr;
     const int dtype = dt == SF_F64 ? 0 : 1;
-    const long long warps_wanted = d.n_parts;
-    long long blocks = (long long)occupancy(mode, dtype, lpr) * S->sms;
-    blocks = std::min<long long>(blocks, (warps_wanted + 7) / 8);
+    void *vbuf = value_flag_buffer(mode, a);
+    const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
+    if (vf) SF_CK(cudaMemsetAsync(vbuf, 0xff, (size_t)S->n * (dt == SF_F64 ? 8 : 4), s), "value-flag reset");
+    int per_sm = occupancy(mode, dtype, lpr, vf);
+    if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
+    long long blocks = (long long)per_sm * S->sms;
+    blocks = std::min<long long>(blocks, ((long long)d.n_parts + 7) / 8);
     blocks = std::max<long long>(blocks, 1);
     cudaError_t e;
-    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, (int)blocks, s, a);
-    else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) e = launch_exec_adj(mode, dtype, lpr, (int)blocks, s, a);
-    else e = launch_exec_pair(mode, dtype, lpr, (int)blocks, s, a);
+    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, (int)blocks, s, a);
+    else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
+        e = launch_exec_adj(mode, dtype, lpr, vf, (int)blocks, s, a);
+    else e = launch_exec_pair(mode, dtype, lpr, vf, (int)blocks, s, a);
     if (e != cudaSuccess) return from_cuda(e, "executor launch");
     return SF_OK;
 }
@@ -655,6 +684,9 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     info->rhs_tile = S->kt;
     info->part_cost_target = S->fwd.C;
     info->packing = S->packing;
+    info->blocks_per_sm = S->blocks_per_sm;
+    info->epoch_flags = S->epoch_flags ? 1 : 0;
+    info->dynamic_queue = S->dynamic_queue ? 1 : 0;
     info->reuse_ratio = S->reuse;
     info->inspect_ms = S->inspect_ms;
     return SF_OK;
@@ -672,15 +704,20 @@ SF_API sf_status sf_schedule_export(const sf_schedule *S, int32_t which, int32_t
     return SF_OK;
 }
 
-SF_API sf_status sf_schedule_set_launch(sf_schedule *S, int32_t lanes_per_row, int32_t rhs_tile) {
+SF_API sf_status sf_schedule_set_launch(sf_schedule *S, int32_t lanes_per_row, int32_t rhs_tile, int32_t blocks_per_sm,
+                                        int32_t epoch_flags) {
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (lanes_per_row && !is_pow2_upto32(lanes_per_row)) return fail(SF_ERR_INVALID_ARG, "bad lanes_per_row");
     if (rhs_tile && !is_pow2_upto32(rhs_tile)) return fail(SF_ERR_INVALID_ARG, "bad rhs_tile");
+    if (blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "bad blocks_per_sm");
+    if (epoch_flags < -1 || epoch_flags > 1) return fail(SF_ERR_INVALID_ARG, "epoch_flags must be -1, 0 or 1");
     const int lpr = lanes_per_row ? lanes_per_row : S->lpr;
     const int kt = rhs_tile ? rhs_tile : S->kt;
     if (kt > lpr) return fail(SF_ERR_INVALID_ARG, "rhs_tile must not exceed lanes_per_row");
     S->lpr = lpr;
     S->kt = kt;
+    if (blocks_per_sm) S->blocks_per_sm = blocks_per_sm;
+    if (epoch_flags >= 0) S->epoch_flags = epoch_flags == 1;
     return SF_OK;
 }
 

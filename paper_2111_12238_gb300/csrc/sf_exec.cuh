@@ -5,26 +5,67 @@
 // repeatedly takes the next partition from a ticket counter and runs its items; a warp is
 // split into 32/LPR groups of LPR lanes, each group running one item (one row of one
 // kernel, or one paired row of both kernels) at a time. Instead of the barrier that
-// separates s-partitions in the paper's executor, every produced row publishes a ready
-// flag with release semantics and every consumer waits on the flags of exactly the rows
-// it reads (its DAG predecessors and F row), so a row starts as soon as its inputs exist.
+// separates s-partitions in the paper's executor, every produced row is published and
+// every consumer waits for exactly the rows it reads (its DAG predecessors and its F
+// row), so a row starts as soon as its inputs exist.
 //
-// Deadlock freedom: tickets are handed out in the topological order, so every item a
-// warp waits on belongs to an earlier partition, whose warp is already running, or to an
-// earlier item of its own partition. Waits are bounded by %globaltimer; on expiry the
-// warp records SF_ERR_TIMEOUT, raises `abort`, and every warp drains.
+// Two publication mechanisms:
+//  * epoch flags (any k): the producer stores its row, then releases flag[row] = epoch;
+//    consumers poll flags with relaxed loads and issue one acquire fence per batch.
+//  * value flags (VF, k = 1): the dependency vector is reset to an all-ones NaN pattern
+//    before the launch; the producer stores the value with one relaxed store and the
+//    consumer polls the value itself, so a hop costs one store and one load.
+// Waits back off exponentially with __nanosleep so that waiting warps neither flood L2
+// with polls nor starve the lanes of their own warp that compute the awaited rows.
+//
+// Work assignment: by default partitions go round robin to the warps of a cooperative
+// (fully co-resident) launch: warp w runs partitions w, w + W, w + 2W, ... in order. With
+// `dynamic` a warp instead draws its next partition from a ticket counter.
+// Deadlock freedom, both cases: partitions are topologically ordered and every warp runs
+// its own partitions in increasing order, so the smallest unfinished partition belongs to
+// a running warp that is working on it (any earlier partition of that warp is finished)
+// and all its dependences lie in smaller, finished partitions or earlier items of its own.
+// Waits are bounded by %globaltimer; on expiry the warp records SF_ERR_TIMEOUT, raises
+// `abort`, and every warp drains.
 #pragma once
 
 #include "sf_internal.cuh"
 
 namespace sf {
 
-template <typename T> struct VT;
-template <> struct VT<double> { static constexpr int id = 0; };
-template <> struct VT<float> { static constexpr int id = 1; };
-
 constexpr int kUnroll = 4;   // row entries fetched per lane before waiting on them
+constexpr unsigned kBackoffMinNs = 20, kBackoffMaxNs = 256;
 
+// ------------------------------------------------------------------ value-flag helpers
+template <typename T> __device__ __forceinline__ T ld_relaxed_val(const T *p);
+template <> __device__ __forceinline__ double ld_relaxed_val<double>(const double *p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+template <> __device__ __forceinline__ float ld_relaxed_val<float>(const float *p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_val(double *p, double v) {
+    asm volatile("st.relaxed.gpu.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_val(float *p, float v) {
+    asm volatile("st.relaxed.gpu.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+// "not yet produced": every bit set (a NaN that arithmetic does not produce)
+__device__ __forceinline__ bool is_unset(double v) { return __double_as_longlong(v) == -1LL; }
+__device__ __forceinline__ bool is_unset(float v) { return __float_as_uint(v) == 0xffffffffu; }
+__device__ __forceinline__ double canonical_nan(double) { return __longlong_as_double(0x7ff8000000000000LL); }
+__device__ __forceinline__ float canonical_nan(float) { return __uint_as_float(0x7fc00000u); }
+template <typename T>
+__device__ __forceinline__ void put_value(T *p, T v) {
+    if (is_unset(v)) v = canonical_nan(v);   // a NaN either way; keep the reset pattern unique
+    st_relaxed_val(p, v);
+}
+
+// ------------------------------------------------------------------ reductions
 // Sum over the lanes of a group that share a right-hand-side column (xor partners at
 // distance >= kt).
 template <int LPR, typename T>
@@ -34,59 +75,96 @@ __device__ __forceinline__ T slice_sum(T v, int kt, unsigned gmask) {
         if (off >= kt) v += __shfl_xor_sync(gmask, v, off);
     return v;
 }
-// Sum over all lanes of a group.
 template <int LPR, typename T>
 __device__ __forceinline__ T group_sum(T v, unsigned gmask) {
 #pragma unroll
     for (int off = LPR / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(gmask, v, off);
     return v;
 }
-// Sum over the kt lanes of one slice (the right-hand-side columns of one entry).
 template <typename T>
 __device__ __forceinline__ T col_sum(T v, int kt, unsigned smask) {
     for (int off = kt >> 1; off >= 1; off >>= 1) v += __shfl_xor_sync(smask, v, off);
     return v;
 }
 
-// Waits until every listed row (j[u] >= 0) is published in this epoch. Flags are polled
-// with relaxed loads so that the polls of one batch are in flight together; one acquire
-// fence after the last poll orders the subsequent data loads after every observed
-// release (fence-acquire pattern). Returns false on abort or timeout.
-template <int U>
-__device__ __forceinline__ bool wait_rows(const unsigned *flags, const int (&j)[U], unsigned epoch,
-                                          ExecState *st, unsigned long long tmo, int row) {
-    unsigned pending = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-        if (j[u] >= 0 && ld_relaxed_u32(flags + j[u]) != epoch) pending |= 1u << u;
-    bool any = false;
-#pragma unroll
-    for (int u = 0; u < U; ++u) any |= j[u] >= 0;
-    if (pending) {
-        const unsigned long long t0 = global_ns();
-        for (unsigned it = 1; pending; ++it) {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if ((pending >> u) & 1u)
-                    if (ld_relaxed_u32(flags + j[u]) == epoch) pending &= ~(1u << u);
-            if (pending && (it & 31u) == 0u) {
-                if (ld_relaxed_u32(&st->abort)) return false;
-                if (global_ns() - t0 > tmo) {
-                    record_error(st, SF_ERR_TIMEOUT, row);
-                    st_relaxed_u32(&st->abort, 1u);
-                    return false;
-                }
+// Bounded wait bookkeeping shared by both mechanisms: sleeps with exponential backoff,
+// checks `abort` and the time limit every 16 rounds.
+struct Waiter {
+    unsigned ns = kBackoffMinNs;
+    unsigned it = 0;
+    unsigned long long t0 = 0;
+    __device__ __forceinline__ bool pause(ExecState *st, unsigned long long tmo, int row) {
+        if (it == 0) t0 = global_ns();
+        __nanosleep(ns);
+        ns = ns < kBackoffMaxNs ? ns * 2 : kBackoffMaxNs;
+        if ((++it & 15u) == 0u) {
+            if (ld_relaxed_u32(&st->abort)) return false;
+            if (global_ns() - t0 > tmo) {
+                record_error(st, SF_ERR_TIMEOUT, row);
+                st_relaxed_u32(&st->abort, 1u);
+                return false;
             }
         }
+        return true;
+    }
+};
+
+// Epoch flags: waits until every listed row (j[u] >= 0) is published in this epoch, then
+// one acquire fence orders the data loads after every observed release.
+template <int U>
+__device__ __forceinline__ bool wait_flags(const unsigned *flags, const int (&j)[U], unsigned epoch,
+                                           ExecState *st, unsigned long long tmo, int row) {
+    unsigned pending = 0;
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        any |= j[u] >= 0;
+        if (j[u] >= 0 && ld_relaxed_u32(flags + j[u]) != epoch) pending |= 1u << u;
+    }
+    Waiter w;
+    while (pending) {
+        if (!w.pause(st, tmo, row)) return false;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (((pending >> u) & 1u) && ld_relaxed_u32(flags + j[u]) == epoch) pending &= ~(1u << u);
     }
     if (any) fence_acq_rel_gpu();
     return true;
 }
 
+// Value flags (k = 1): loads vec[j[u]] until it is no longer the reset pattern.
+template <typename T, int U>
+__device__ __forceinline__ bool wait_values(const T *vec, const int (&j)[U], T (&xv)[U], ExecState *st,
+                                            unsigned long long tmo, int row) {
+    unsigned pending = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        xv[u] = T(0);
+        if (j[u] >= 0) {
+            xv[u] = ld_relaxed_val(vec + j[u]);
+            if (is_unset(xv[u])) pending |= 1u << u;
+        }
+    }
+    Waiter w;
+    while (pending) {
+        if (!w.pause(st, tmo, row)) return false;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if ((pending >> u) & 1u) {
+                xv[u] = ld_relaxed_val(vec + j[u]);
+                if (!is_unset(xv[u])) pending &= ~(1u << u);
+            }
+    }
+    return true;
+}
+
+// Dependency mode of a row dot product.
+enum Dep { D_NONE = 0, D_FLAG = 1, D_VALUE = 2 };
+
 // acc = sum over this lane's slice of entries e in [e0, e1) (stride S) of
-// vals[PERM ? perm[e] : e] * vec[cols[e] * k + c]. With WAIT the rows cols[e] are waited
-// for first and vec is read through L2 (it is produced by other warps in this launch).
-template <typename T, bool WAIT, bool PERM>
+// vals[PERM ? perm[e] : e] * vec[cols[e] * k + c]. D_FLAG / D_VALUE wait for the rows
+// cols[e] first (vec is produced by other warps in this launch).
+template <typename T, int DEP, bool PERM>
 __device__ __forceinline__ T row_dot(const int *__restrict__ cols, const int *__restrict__ perm,
                                      const T *__restrict__ vals, int e0, int e1, int S, const T *vec,
                                      int k, int c, bool act, const unsigned *flags, unsigned epoch,
@@ -105,24 +183,33 @@ __device__ __forceinline__ T row_dot(const int *__restrict__ cols, const int *__
                 v[u] = __ldg(vals + (PERM ? __ldg(perm + ee) : ee));
             }
         }
-        if (WAIT && ok) ok = wait_rows<kUnroll>(flags, j, epoch, st, tmo, row);
-        if (act) {
+        if constexpr (DEP == D_VALUE) {
+            T xv[kUnroll];
+            if (ok) ok = wait_values<T, kUnroll>(vec, j, xv, st, tmo, row);
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
-                if (j[u] >= 0) {
-                    const T xv = WAIT ? __ldcg(vec + (size_t)j[u] * k + c) : __ldg(vec + (size_t)j[u] * k + c);
-                    acc += v[u] * xv;
-                }
+                if (j[u] >= 0) acc += v[u] * xv[u];
+        } else {
+            if (DEP == D_FLAG && ok) ok = wait_flags<kUnroll>(flags, j, epoch, st, tmo, row);
+            if (act) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+                    if (j[u] >= 0) {
+                        const T xv = DEP == D_FLAG ? __ldcg(vec + (size_t)j[u] * k + c)
+                                                   : __ldg(vec + (size_t)j[u] * k + c);
+                        acc += v[u] * xv;
+                    }
+            }
         }
     }
     return acc;
 }
 
-// out[e] = sign * sum_c coef[c] * vec[cols[e] * k + c] for e in [e0, e1): the pattern-
-// restricted outer product of the adjoint gradients. Lanes: slice s = gl / kt takes
-// every S-th entry, its kt lanes split the right-hand-side columns.
-template <typename T, int LPR>
-__device__ __forceinline__ void grad_row(const int *__restrict__ cols, int e0, int e1, const T *coef,
+// out[e] = sign * sum_c coef(c) * vec[cols[e] * k + c] for e in [e0, e1): the pattern-
+// restricted outer product of the adjoint gradients. Slice s = gl / kt takes every S-th
+// entry, its kt lanes split the right-hand-side columns.
+template <typename T, int LPR, typename Coef>
+__device__ __forceinline__ void grad_row(const int *__restrict__ cols, int e0, int e1, Coef coef,
                                          const T *__restrict__ vec, int k, int kt, int gl, int gbase,
                                          T sign, T *out) {
     const int S = LPR / kt, s = gl / kt, cl = gl % kt;
@@ -130,7 +217,7 @@ __device__ __forceinline__ void grad_row(const int *__restrict__ cols, int e0, i
     for (int e = e0 + s; e < e1; e += S) {
         const int j = __ldg(cols + e);
         T part = T(0);
-        for (int c = cl; c < k; c += kt) part += coef[c] * __ldg(vec + (size_t)j * k + c);
+        for (int c = cl; c < k; c += kt) part += coef(c) * __ldg(vec + (size_t)j * k + c);
         part = col_sum(part, kt, smask);
         if (cl == 0) out[e] = sign * part;
     }
@@ -141,20 +228,27 @@ __device__ __forceinline__ bool group_ok(bool ok, unsigned gmask) {
     return !__any_sync(gmask, !ok);
 }
 
-template <int LPR>
-__device__ __forceinline__ void publish(const ExecArgs &a, int row, unsigned epoch, int gl,
-                                        unsigned gmask, bool ok) {
+// Epoch-flag publication of a row written by the lanes of a group.
+__device__ __forceinline__ void publish(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask,
+                                        bool ok) {
     __syncwarp(gmask);
     if (gl == 0 && ok) st_release_u32(a.flags + row, epoch);
+}
+
+// Writes one produced value: with value flags the store itself publishes it.
+template <bool VF, typename T>
+__device__ __forceinline__ void store_out(T *p, T v) {
+    if (VF) put_value(p, v);
+    else *p = v;
 }
 
 // ---------------------------------------------------------------- item kinds
 // SpTRSV row (Table 2, forward substitution): x_i = (b_i - sum_{j<i} L_ij x_j) / L_ii.
 // `x` is both the output and the buffer the dependences are read from.
-template <typename T, int LPR>
+template <typename T, int LPR, bool VF>
 __device__ bool item_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask, T *x) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
-    const int rs = a.Lrp[row], dg = a.Lrp[row + 1] - 1;
+    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Lv = (const T *)a.Lv, *b = (const T *)a.b;
     const T d = __ldg(Lv + dg);
     if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, row);
@@ -162,30 +256,30 @@ __device__ bool item_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, un
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T acc = row_dot<T, true, false>(a.Lci, nullptr, Lv, rs + s, dg, S, x, k, c, act, a.flags, epoch,
-                                        a.st, a.timeout_ns, row, ok);
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Lci, nullptr, Lv, rs + s, dg, S, x, k, c, act, a.flags,
+                                                         epoch, a.st, a.timeout_ns, row, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
-        if (s == 0 && act) x[(size_t)row * k + c] = (__ldg(b + (size_t)row * k + c) - acc) / d;
+        if (s == 0 && act) store_out<VF>(x + (size_t)row * k + c, (__ldg(b + (size_t)row * k + c) - acc) / d);
     }
     ok = group_ok<LPR>(ok, gmask);
-    publish<LPR>(a, row, epoch, gl, gmask, ok);
+    if (!VF) publish(a, row, epoch, gl, gmask, ok);
     return ok;
 }
 
 // SpMV row of the second kernel with F = pattern(M): y_i = sum_j M_ij x_j, each x_j
 // waited for (§2.2 "Dependency Matrix F": row i of F lists the first-kernel iterations
 // row i of the second kernel reads).
-template <typename T, int LPR>
+template <typename T, int LPR, bool VF>
 __device__ bool item_spmv_dep(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask, const T *x) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
-    const int rs = a.Mrp[row], re = a.Mrp[row + 1];
+    const int rs = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1);
     T *y = (T *)a.y;
     bool ok = true;
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T acc = row_dot<T, true, false>(a.Mci, nullptr, (const T *)a.Mv, rs + s, re, S, x, k, c, act, a.flags,
-                                        epoch, a.st, a.timeout_ns, row, ok);
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Mci, nullptr, (const T *)a.Mv, rs + s, re, S, x, k, c,
+                                                         act, a.flags, epoch, a.st, a.timeout_ns, row, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
         if (s == 0 && act) y[(size_t)row * k + c] = acc;
     }
@@ -194,11 +288,11 @@ __device__ bool item_spmv_dep(const ExecArgs &a, int row, unsigned epoch, int gl
 
 // Paired SpMV -> SpTRSV row (combination 2, F = I): r_i = b_i - A_i x_in stays in
 // registers, then z_i = (r_i - sum_{j<i} L_ij z_j) / L_ii.
-template <typename T, int LPR>
+template <typename T, int LPR, bool VF>
 __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
-    const int ra = a.Mrp[row], re = a.Mrp[row + 1];
-    const int rs = a.Lrp[row], dg = a.Lrp[row + 1] - 1;
+    const int ra = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1);
+    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Lv = (const T *)a.Lv, *b = (const T *)a.b;
     T *z = (T *)a.y;
     const T d = __ldg(Lv + dg);
@@ -207,29 +301,29 @@ __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int g
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T accA = row_dot<T, false, false>(a.Mci, nullptr, (const T *)a.Mv, ra + s, re, S, (const T *)a.xin, k, c,
-                                          act, a.flags, epoch, a.st, a.timeout_ns, row, ok);
-        T accL = row_dot<T, true, false>(a.Lci, nullptr, Lv, rs + s, dg, S, z, k, c, act, a.flags, epoch, a.st,
-                                         a.timeout_ns, row, ok);
+        T accA = row_dot<T, D_NONE, false>(a.Mci, nullptr, (const T *)a.Mv, ra + s, re, S, (const T *)a.xin, k, c,
+                                           act, a.flags, epoch, a.st, a.timeout_ns, row, ok);
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Lci, nullptr, Lv, rs + s, dg, S, z, k, c, act, a.flags,
+                                                          epoch, a.st, a.timeout_ns, row, ok);
         accA = slice_sum<LPR>(accA, kt, gmask);
         accL = slice_sum<LPR>(accL, kt, gmask);
         if (s == 0 && act) {
             const T r = __ldg(b + (size_t)row * k + c) - accA;
-            z[(size_t)row * k + c] = (r - accL) / d;
+            store_out<VF>(z + (size_t)row * k + c, (r - accL) / d);
         }
     }
     ok = group_ok<LPR>(ok, gmask);
-    publish<LPR>(a, row, epoch, gl, gmask, ok);
+    if (!VF) publish(a, row, epoch, gl, gmask, ok);
     return ok;
 }
 
 // Paired SpIC0 -> SpTRSV row (combination 5, F = I), IC0 in its up-looking row form:
 // for each j < i in row i, ascending, L_ij = (A_ij - sum_{k<j, k in both rows} L_ik L_jk)
 // / L_jj; then L_ii = sqrt(A_ii - sum_{k<i} L_ik^2); then the solve row with the fresh
-// L_i stays on chip: y_i = (b_i - sum_j L_ij y_j) / L_ii. Factor values go to a.xs.
+// L_i on chip: y_i = (b_i - sum_j L_ij y_j) / L_ii. Factor values go to a.xs.
 template <typename T, int LPR, bool SOLVE>
 __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
-    const int rs = a.Lrp[row], dg = a.Lrp[row + 1] - 1;
+    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Av = (const T *)a.Lv;
     T *lf = (T *)a.xs;
     bool ok = true;
@@ -241,7 +335,7 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
             const int ee = e + u * LPR;
             j[u] = ee < dg ? __ldg(a.Lci + ee) : -1;
         }
-        if (ok) ok = wait_rows<kUnroll>(a.flags, j, epoch, a.st, a.timeout_ns, row);
+        if (ok) ok = wait_flags<kUnroll>(a.flags, j, epoch, a.st, a.timeout_ns, row);
     }
     ok = group_ok<LPR>(ok, gmask);
     for (int t = rs; t < dg; ++t) {
@@ -286,7 +380,7 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
             if (s == 0 && c < k) y[(size_t)row * k + c] = (__ldg(b + (size_t)row * k + c) - acc) / lii;
         }
     }
-    publish<LPR>(a, row, epoch, gl, gmask, ok);
+    publish(a, row, epoch, gl, gmask, ok);
     return ok;
 }
 
@@ -294,110 +388,144 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
 // j of L): u_j = (M^T gy)_j needs no wait; lam_j = (u_j - sum_{i>j} L_ij lam_i) / L_jj
 // waits for lam_i; gb = lam. After publishing, the row's gradients:
 // gL_j* = -lam_j x_*, gM_j* = gy_j x_*.
-template <typename T, int LPR>
+template <typename T, int LPR, bool VF>
 __device__ bool item_adj_trsv_spmv(const ExecArgs &a, int j, unsigned epoch, int gl, int gbase, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
-    const int ms = a.MTrp[j], me = a.MTrp[j + 1];
-    const int ls = a.LTrp[j], le = a.LTrp[j + 1];     // first entry of L^T row j is L_jj
+    const int ms = __ldg(a.MTrp + j), me = __ldg(a.MTrp + j + 1);
+    const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);   // first entry of L^T row j is L_jj
     const T *Lv = (const T *)a.Lv, *gy = (const T *)a.gy, *x = (const T *)a.saved;
     T *lam = (T *)a.gb;
     const T d = __ldg(Lv + __ldg(a.LTperm + ls));
     if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, j);
     bool ok = true;
+    T lam0 = T(0);
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T u = row_dot<T, false, true>(a.MTci, a.MTperm, (const T *)a.Mv, ms + s, me, S, gy, k, c, act, a.flags,
-                                      epoch, a.st, a.timeout_ns, j, ok);
-        T accL = row_dot<T, true, true>(a.LTci, a.LTperm, Lv, ls + 1 + s, le, S, lam, k, c, act, a.flags, epoch,
-                                        a.st, a.timeout_ns, j, ok);
+        T u = row_dot<T, D_NONE, true>(a.MTci, a.MTperm, (const T *)a.Mv, ms + s, me, S, gy, k, c, act, a.flags,
+                                       epoch, a.st, a.timeout_ns, j, ok);
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, true>(a.LTci, a.LTperm, Lv, ls + 1 + s, le, S, lam, k, c, act,
+                                                         a.flags, epoch, a.st, a.timeout_ns, j, ok);
         u = slice_sum<LPR>(u, kt, gmask);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        if (s == 0 && act) lam[(size_t)j * k + c] = (u - accL) / d;
+        const T v = (u - accL) / d;
+        if (c0 == 0) lam0 = v;
+        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, v);
     }
     ok = group_ok<LPR>(ok, gmask);
-    publish<LPR>(a, j, epoch, gl, gmask, ok);
-    if (ok && a.gL)
-        grad_row<T, LPR>(a.Lci, a.Lrp[j], a.Lrp[j + 1], lam + (size_t)j * k, x, k, kt, gl, gbase, T(-1), (T *)a.gL);
-    if (ok && a.gM)
-        grad_row<T, LPR>(a.Mci, a.Mrp[j], a.Mrp[j + 1], gy + (size_t)j * k, x, k, kt, gl, gbase, T(1), (T *)a.gM);
-    return ok;
+    if (!VF) publish(a, j, epoch, gl, gmask, ok);
+    if (!ok) return false;
+    if (VF) {   // k = 1: lam_j is in every lane's registers (slice sums are group-wide)
+        if (a.gL) grad_row<T, LPR>(a.Lci, __ldg(a.Lrp + j), __ldg(a.Lrp + j + 1), [&](int) { return lam0; }, x, k, kt,
+                                   gl, gbase, T(-1), (T *)a.gL);
+    } else {
+        __syncwarp(gmask);
+        const T *lr = lam + (size_t)j * k;
+        if (a.gL) grad_row<T, LPR>(a.Lci, __ldg(a.Lrp + j), __ldg(a.Lrp + j + 1), [&](int c) { return lr[c]; }, x, k,
+                                   kt, gl, gbase, T(-1), (T *)a.gL);
+    }
+    if (a.gM) {
+        const T *gr = gy + (size_t)j * k;
+        grad_row<T, LPR>(a.Mci, __ldg(a.Mrp + j), __ldg(a.Mrp + j + 1), [&](int c) { return __ldg(gr + c); }, x, k,
+                         kt, gl, gbase, T(1), (T *)a.gM);
+    }
+    return true;
 }
 
 // Adjoint of SpMV -> SpTRSV, tag 0: lam_j = (gz_j - sum_{i>j} L_ij lam_i) / L_jj, gb = lam,
 // then gL_j* = -lam_j z_*, gA_j* = -lam_j x_in_*.
-template <typename T, int LPR>
+template <typename T, int LPR, bool VF>
 __device__ bool item_adj_lam(const ExecArgs &a, int j, unsigned epoch, int gl, int gbase, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
-    const int ls = a.LTrp[j], le = a.LTrp[j + 1];
+    const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);
     const T *Lv = (const T *)a.Lv, *gz = (const T *)a.gy;
     T *lam = (T *)a.gb;
     const T d = __ldg(Lv + __ldg(a.LTperm + ls));
     if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, j);
     bool ok = true;
+    T lam0 = T(0);
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T accL = row_dot<T, true, true>(a.LTci, a.LTperm, Lv, ls + 1 + s, le, S, lam, k, c, act, a.flags, epoch,
-                                        a.st, a.timeout_ns, j, ok);
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, true>(a.LTci, a.LTperm, Lv, ls + 1 + s, le, S, lam, k, c, act,
+                                                         a.flags, epoch, a.st, a.timeout_ns, j, ok);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        if (s == 0 && act) lam[(size_t)j * k + c] = (__ldg(gz + (size_t)j * k + c) - accL) / d;
+        const T v = act ? (__ldg(gz + (size_t)j * k + c) - accL) / d : T(0);
+        if (c0 == 0) lam0 = v;
+        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, v);
     }
     ok = group_ok<LPR>(ok, gmask);
-    publish<LPR>(a, j, epoch, gl, gmask, ok);
-    if (ok && a.gL)
-        grad_row<T, LPR>(a.Lci, a.Lrp[j], a.Lrp[j + 1], lam + (size_t)j * k, (const T *)a.saved, k, kt, gl, gbase,
+    if (!VF) publish(a, j, epoch, gl, gmask, ok);
+    if (!ok) return false;
+    const T *lr = lam + (size_t)j * k;
+    if (!VF) __syncwarp(gmask);
+    auto coef = [&](int c) { return VF ? lam0 : lr[c]; };
+    if (a.gL)
+        grad_row<T, LPR>(a.Lci, __ldg(a.Lrp + j), __ldg(a.Lrp + j + 1), coef, (const T *)a.saved, k, kt, gl, gbase,
                          T(-1), (T *)a.gL);
-    if (ok && a.gM)
-        grad_row<T, LPR>(a.Mci, a.Mrp[j], a.Mrp[j + 1], lam + (size_t)j * k, (const T *)a.xin, k, kt, gl, gbase,
+    if (a.gM)
+        grad_row<T, LPR>(a.Mci, __ldg(a.Mrp + j), __ldg(a.Mrp + j + 1), coef, (const T *)a.xin, k, kt, gl, gbase,
                          T(-1), (T *)a.gM);
-    return ok;
+    return true;
 }
 
 // Adjoint of SpMV -> SpTRSV, tag 1: gx_j = -sum_i A_ij lam_i, waiting for each lam_i.
-template <typename T, int LPR>
+template <typename T, int LPR, bool VF>
 __device__ bool item_adj_gx(const ExecArgs &a, int j, unsigned epoch, int gl, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
-    const int ms = a.MTrp[j], me = a.MTrp[j + 1];
+    const int ms = __ldg(a.MTrp + j), me = __ldg(a.MTrp + j + 1);
     T *gx = (T *)a.gx;
     bool ok = true;
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T acc = row_dot<T, true, true>(a.MTci, a.MTperm, (const T *)a.Mv, ms + s, me, S, (const T *)a.gb, k, c,
-                                       act, a.flags, epoch, a.st, a.timeout_ns, j, ok);
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, true>(a.MTci, a.MTperm, (const T *)a.Mv, ms + s, me, S,
+                                                        (const T *)a.gb, k, c, act, a.flags, epoch, a.st,
+                                                        a.timeout_ns, j, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
         if (s == 0 && act) gx[(size_t)j * k + c] = -acc;
     }
     return group_ok<LPR>(ok, gmask);
 }
 
-template <int MODE, typename T, int LPR>
+// Modes whose k = 1 launches use value flags.
+constexpr bool mode_has_vf(int m) {
+    return m == M_TRSV_SPMV || m == M_TRSV || m == M_SPMV_TRSV || m == M_ADJ_TRSV_SPMV || m == M_ADJ_SPMV_TRSV;
+}
+
+template <int MODE, typename T, int LPR, bool VF>
 __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, unsigned epoch, int gl, int gbase,
                                          unsigned gmask) {
     if constexpr (MODE == M_TRSV_SPMV) {
-        if (tag == 0) return item_trsv<T, LPR>(a, row, epoch, gl, gmask, (T *)a.xs);
-        return item_spmv_dep<T, LPR>(a, row, epoch, gl, gmask, (const T *)a.xs);
+        if (tag == 0) return item_trsv<T, LPR, VF>(a, row, epoch, gl, gmask, (T *)a.xs);
+        return item_spmv_dep<T, LPR, VF>(a, row, epoch, gl, gmask, (const T *)a.xs);
     } else if constexpr (MODE == M_TRSV) {
-        return item_trsv<T, LPR>(a, row, epoch, gl, gmask, (T *)a.y);
+        return item_trsv<T, LPR, VF>(a, row, epoch, gl, gmask, (T *)a.y);
     } else if constexpr (MODE == M_SPMV_TRSV) {
-        return item_spmv_trsv<T, LPR>(a, row, epoch, gl, gmask);
+        return item_spmv_trsv<T, LPR, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0_TRSV) {
         return item_ic0<T, LPR, true>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0) {
         return item_ic0<T, LPR, false>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_ADJ_TRSV_SPMV) {
-        return item_adj_trsv_spmv<T, LPR>(a, row, epoch, gl, gbase, gmask);
+        return item_adj_trsv_spmv<T, LPR, VF>(a, row, epoch, gl, gbase, gmask);
     } else {
-        if (tag == 0) return item_adj_lam<T, LPR>(a, row, epoch, gl, gbase, gmask);
+        if (tag == 0) return item_adj_lam<T, LPR, VF>(a, row, epoch, gl, gbase, gmask);
         if (!a.gx) return true;    // gradient of x_in not requested
-        return item_adj_gx<T, LPR>(a, row, epoch, gl, gmask);
+        return item_adj_gx<T, LPR, VF>(a, row, epoch, gl, gmask);
     }
 }
 
 constexpr int kExecThreads = 256;
 
-template <int MODE, typename T, int LPR>
+// Next ticket of a warp (lane 0 draws it; the caller broadcasts it when needed, so the
+// atomic's latency overlaps the current partition's work).
+__device__ __forceinline__ int draw_ticket(const ExecArgs &a, int lane) {
+    if (lane != 0) return 0;
+    return ld_relaxed_u32(&a.st->abort) ? a.n_parts : (int)atomicAdd(&a.st->ticket, 1u);
+}
+
+template <int MODE, typename T, int LPR, bool VF>
 __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecArgs a) {
     constexpr int G = 32 / LPR;
     const int lane = threadIdx.x & 31;
@@ -405,17 +533,22 @@ __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecArgs a) {
     const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << gbase);
     const unsigned epoch = ld_relaxed_u32(&a.st->epoch);
     bool ok = true;
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : (int)atomicAdd(&a.st->ticket, 1u);
-        p = __shfl_sync(0xffffffffu, p, 0);
-        if (p >= a.n_parts) break;
+    // A warp holds its current partition and the ticket of its next one. Both are drawn
+    // in ticket order, so the smallest unfinished partition held by any warp is always a
+    // current one whose dependences are all finished: progress is preserved.
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int p = a.dynamic ? __shfl_sync(0xffffffffu, draw_ticket(a, lane), 0) : wid;
+    while (p < a.n_parts) {
+        const int pn_lane0 = a.dynamic ? draw_ticket(a, lane) : 0;
         const int q0 = __ldg(a.part_ptr + p), q1 = __ldg(a.part_ptr + p + 1);
         for (int q = q0 + grp; q < q1 && ok; q += G) {
             const unsigned o = (unsigned)__ldg(a.order + q);
-            ok = run_item<MODE, T, LPR>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
+            ok = run_item<MODE, T, LPR, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
         }
         if (!__all_sync(0xffffffffu, ok)) break;
+        if (a.dynamic) p = __shfl_sync(0xffffffffu, pn_lane0, 0);
+        else p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : p + nwarps;
     }
     __syncwarp();
     if (lane == 0) {
@@ -429,50 +562,52 @@ __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecArgs a) {
     }
 }
 
-// Instantiates and launches k_exec<MODE, T, LPR> for a runtime (dtype, lanes-per-row).
-template <int MODE>
-cudaError_t launch_mode(int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a) {
-#define SF_LAUNCH(T, L) k_exec<MODE, T, L><<<blocks, kExecThreads, 0, s>>>(a); return cudaGetLastError()
+template <int MODE, bool VF>
+const void *kernel_for(int dtype, int lpr) {
     if (dtype == 0) {
         switch (lpr) {
-            case 1: SF_LAUNCH(double, 1);
-            case 2: SF_LAUNCH(double, 2);
-            case 4: SF_LAUNCH(double, 4);
-            case 8: SF_LAUNCH(double, 8);
-            case 16: SF_LAUNCH(double, 16);
-            case 32: SF_LAUNCH(double, 32);
+            case 1: return (const void *)k_exec<MODE, double, 1, VF>;
+            case 2: return (const void *)k_exec<MODE, double, 2, VF>;
+            case 4: return (const void *)k_exec<MODE, double, 4, VF>;
+            case 8: return (const void *)k_exec<MODE, double, 8, VF>;
+            case 16: return (const void *)k_exec<MODE, double, 16, VF>;
+            case 32: return (const void *)k_exec<MODE, double, 32, VF>;
         }
     } else {
         switch (lpr) {
-            case 1: SF_LAUNCH(float, 1);
-            case 2: SF_LAUNCH(float, 2);
-            case 4: SF_LAUNCH(float, 4);
-            case 8: SF_LAUNCH(float, 8);
-            case 16: SF_LAUNCH(float, 16);
-            case 32: SF_LAUNCH(float, 32);
+            case 1: return (const void *)k_exec<MODE, float, 1, VF>;
+            case 2: return (const void *)k_exec<MODE, float, 2, VF>;
+            case 4: return (const void *)k_exec<MODE, float, 4, VF>;
+            case 8: return (const void *)k_exec<MODE, float, 8, VF>;
+            case 16: return (const void *)k_exec<MODE, float, 16, VF>;
+            case 32: return (const void *)k_exec<MODE, float, 32, VF>;
         }
     }
-#undef SF_LAUNCH
-    return cudaErrorInvalidValue;
+    return nullptr;
 }
 
 template <int MODE>
-int blocks_per_sm_mode(int dtype, int lpr) {
-    int nb = 0;
-    const void *f = nullptr;
-#define SF_F(T, L) f = (const void *)k_exec<MODE, T, L>; break
-    if (dtype == 0) {
-        switch (lpr) {
-            case 1: SF_F(double, 1); case 2: SF_F(double, 2); case 4: SF_F(double, 4);
-            case 8: SF_F(double, 8); case 16: SF_F(double, 16); case 32: SF_F(double, 32);
-        }
-    } else {
-        switch (lpr) {
-            case 1: SF_F(float, 1); case 2: SF_F(float, 2); case 4: SF_F(float, 4);
-            case 8: SF_F(float, 8); case 16: SF_F(float, 16); case 32: SF_F(float, 32);
-        }
+const void *kernel_for_mode(int dtype, int lpr, bool vf) {
+    if constexpr (mode_has_vf(MODE)) {
+        if (vf) return kernel_for<MODE, true>(dtype, lpr);
     }
-#undef SF_F
+    return kernel_for<MODE, false>(dtype, lpr);
+}
+
+// Launches k_exec<MODE, T, LPR, VF> for a runtime (dtype, lanes-per-row, value flags).
+template <int MODE>
+cudaError_t launch_mode(int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a) {
+    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf);
+    if (!f) return cudaErrorInvalidValue;
+    void *args[] = {(void *)&a};
+    if (a.dynamic) return cudaLaunchKernel(f, dim3(blocks), dim3(kExecThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(kExecThreads), args, 0, s);
+}
+
+template <int MODE>
+int blocks_per_sm_mode(int dtype, int lpr, bool vf) {
+    int nb = 0;
+    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf);
     if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kExecThreads, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }

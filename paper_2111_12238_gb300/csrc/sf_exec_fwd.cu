@@ -4,15 +4,15 @@
 
 namespace sf {
 
-cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a) {
-    if (mode == M_TRSV_SPMV) return launch_mode<M_TRSV_SPMV>(dtype, lpr, blocks, s, a);
-    if (mode == M_TRSV) return launch_mode<M_TRSV>(dtype, lpr, blocks, s, a);
+cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a) {
+    if (mode == M_TRSV_SPMV) return launch_mode<M_TRSV_SPMV>(dtype, lpr, vf, blocks, s, a);
+    if (mode == M_TRSV) return launch_mode<M_TRSV>(dtype, lpr, vf, blocks, s, a);
     return cudaErrorInvalidValue;
 }
 
-int occupancy_fwd(int mode, int dtype, int lpr) {
-    if (mode == M_TRSV_SPMV) return blocks_per_sm_mode<M_TRSV_SPMV>(dtype, lpr);
-    return blocks_per_sm_mode<M_TRSV>(dtype, lpr);
+int occupancy_fwd(int mode, int dtype, int lpr, bool vf) {
+    if (mode == M_TRSV_SPMV) return blocks_per_sm_mode<M_TRSV_SPMV>(dtype, lpr, vf);
+    return blocks_per_sm_mode<M_TRSV>(dtype, lpr, vf);
 }
 
 // y = M x or y = b - M x, one group of LPR lanes per row, rows in order (no
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_spmv(int nrows, int k, int kt, const in
         for (int c0 = 0; c0 < k; c0 += kt) {
             const int c = c0 + cl;
             const bool act = c < k;
-            T acc = row_dot<T, false, false>(ci, nullptr, v, rs + s, re, S, x, k, c, act, nullptr, 0u, nullptr,
+            T acc = row_dot<T, D_NONE, false>(ci, nullptr, v, rs + s, re, S, x, k, c, act, nullptr, 0u, nullptr,
                                              0ull, (int)row, dummy);
             acc = slice_sum<LPR>(acc, kt, gmask);
             if (s == 0 && act) {

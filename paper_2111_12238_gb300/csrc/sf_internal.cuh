@@ -51,6 +51,7 @@ struct ExecArgs {
     int n;
     int k;
     int kt;                 // right-hand-side columns handled side by side (pow2 <= lanes)
+    int dynamic;            // 1: partitions from a ticket counter; 0: static round robin
     unsigned *flags;
     ExecState *st;
     unsigned long long timeout_ns;
@@ -63,12 +64,13 @@ struct ExecArgs {
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
-cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a);
-cudaError_t launch_exec_pair(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a);
-cudaError_t launch_exec_adj(int mode, int dtype, int lpr, int blocks, cudaStream_t s, const ExecArgs &a);
-int occupancy_fwd(int mode, int dtype, int lpr);
-int occupancy_pair(int mode, int dtype, int lpr);
-int occupancy_adj(int mode, int dtype, int lpr);
+// Static assignment needs every block resident: those launches are cooperative.
+cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a);
+cudaError_t launch_exec_pair(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a);
+cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a);
+int occupancy_fwd(int mode, int dtype, int lpr, bool vf);
+int occupancy_pair(int mode, int dtype, int lpr, bool vf);
+int occupancy_adj(int mode, int dtype, int lpr, bool vf);
 cudaError_t launch_spmv(int dtype, int lpr, int kt, int nrows, int k, const int *rp, const int *ci,
                         const void *v, const void *x, const void *b, void *y, cudaStream_t s);
 

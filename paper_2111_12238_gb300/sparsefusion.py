@@ -21,6 +21,8 @@ from . import _build
 
 PAIRS = {"trsv_spmv": 0, "ic0_trsv": 1, "spmv_trsv": 2, "trsv": 3, "ic0": 4}
 SF_WANT_ADJOINT = 0x1
+SF_EPOCH_FLAGS = 0x2
+SF_DYNAMIC_QUEUE = 0x4
 STATUS = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_BAD_PATTERN", 3: "SF_ERR_CUDA", 4: "SF_ERR_OOM",
           5: "SF_ERR_TIMEOUT", 6: "SF_ERR_BREAKDOWN", 7: "SF_ERR_NONFINITE", 8: "SF_ERR_UNSUPPORTED"}
 
@@ -32,7 +34,7 @@ class SfCsr(C.Structure):
 
 class SfOptions(C.Structure):
     _fields_ = [("part_cost_target", C.c_int64), ("lanes_per_row", C.c_int32), ("rhs_tile", C.c_int32),
-                ("g2_placement", C.c_int32), ("reserved", C.c_int32), ("timeout_ns", C.c_uint64),
+                ("g2_placement", C.c_int32), ("blocks_per_sm", C.c_int32), ("timeout_ns", C.c_uint64),
                 ("flags", C.c_uint32), ("reserved2", C.c_uint32)]
 
 
@@ -42,7 +44,8 @@ class SfInfo(C.Structure):
                 ("adj_depth", C.c_int32), ("adj_n_parts", C.c_int32), ("adj_n_items", C.c_int64),
                 ("lanes_per_row", C.c_int32), ("rhs_tile", C.c_int32),
                 ("part_cost_target", C.c_int64), ("adj_part_cost_target", C.c_int64),
-                ("packing", C.c_int32), ("reserved", C.c_int32),
+                ("packing", C.c_int32), ("blocks_per_sm", C.c_int32), ("epoch_flags", C.c_int32),
+                ("dynamic_queue", C.c_int32),
                 ("reuse_ratio", C.c_double), ("inspect_ms", C.c_double)]
 
 
@@ -69,7 +72,7 @@ _SIGS = {
     "sf_schedule_info": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "sf_schedule_query": (C.c_int, [_P, C.POINTER(SfInfo)]),
     "sf_schedule_export": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
-    "sf_schedule_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "sf_schedule_set_timeout": (C.c_int, [_P, C.c_uint64]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
@@ -168,13 +171,16 @@ class DeviceCsr:
                      self.colidx.data_ptr() if self.nnz else 0)
 
 
-def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns) -> SfOptions:
+def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm=0,
+             epoch_flags=False, dynamic_queue=False) -> SfOptions:
     o = SfOptions()
     o.part_cost_target = int(part_cost_target)
     o.lanes_per_row = int(lanes_per_row)
     o.rhs_tile = int(rhs_tile)
     o.timeout_ns = int(timeout_ns)
-    o.flags = SF_WANT_ADJOINT if want_adjoint else 0
+    o.blocks_per_sm = int(blocks_per_sm)
+    o.flags = ((SF_WANT_ADJOINT if want_adjoint else 0) | (SF_EPOCH_FLAGS if epoch_flags else 0)
+               | (SF_DYNAMIC_QUEUE if dynamic_queue else 0))
     return o
 
 
@@ -237,8 +243,9 @@ class Schedule:
         st = load_library().sf_schedule_check(self.handle, _stream(stream), C.byref(row))
         return st, row.value
 
-    def set_launch(self, lanes_per_row=0, rhs_tile=0):
-        _check(load_library().sf_schedule_set_launch(self.handle, int(lanes_per_row), int(rhs_tile)),
+    def set_launch(self, lanes_per_row=0, rhs_tile=0, blocks_per_sm=0, epoch_flags=-1):
+        _check(load_library().sf_schedule_set_launch(self.handle, int(lanes_per_row), int(rhs_tile),
+                                                     int(blocks_per_sm), int(epoch_flags)),
                "sf_schedule_set_launch")
 
     def set_timeout(self, ns: int):
@@ -277,9 +284,11 @@ class Schedule:
 
 
 def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjoint=False, part_cost_target=0,
-            lanes_per_row=0, rhs_tile=0, timeout_ns=0, stream=None) -> Schedule:
+            lanes_per_row=0, rhs_tile=0, timeout_ns=0, blocks_per_sm=0, epoch_flags=False,
+            dynamic_queue=False, stream=None) -> Schedule:
     lib = load_library()
-    o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns)
+    o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
+                 dynamic_queue)
     Ls = L.struct()
     Ms = M.struct() if M is not None else None
     h = C.c_void_p()
@@ -291,9 +300,10 @@ def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjo
 
 def inspect_batched(pair: str, Ls: Sequence[DeviceCsr], Ms: Optional[Sequence[DeviceCsr]] = None, *,
                     want_adjoint=False, part_cost_target=0, lanes_per_row=0, rhs_tile=0, timeout_ns=0,
-                    stream=None) -> Schedule:
+                    blocks_per_sm=0, epoch_flags=False, dynamic_queue=False, stream=None) -> Schedule:
     lib = load_library()
-    o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns)
+    o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
+                 dynamic_queue)
     cnt = len(Ls)
     la = (SfCsr * cnt)(*[x.struct() for x in Ls])
     ma = (SfCsr * cnt)(*[x.struct() for x in Ms]) if Ms is not None else None

@@ -14,14 +14,15 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("k", [1, 4, 32])
+@pytest.mark.parametrize("k,ef", [(1, False), (1, True), (4, False), (32, False)])
 @pytest.mark.parametrize("lpr", [0, 1, 32])
-def test_adjoint_trsv_spmv(dtype, k, lpr):
+def test_adjoint_trsv_spmv(dtype, k, ef, lpr):
     need_cuda()
     w = I.trsv_spmv_lap3d_band(11, per_row=6, halfband=150, seed=41, k=k)
     x_ref, _ = oracle.trsv_spmv(w.L, w.M, w.b)
     gb_ref, gL_ref, gM_ref = oracle.adj_trsv_spmv(w.L, w.M, x_ref, w.gy)
-    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, lanes_per_row=lpr)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, lanes_per_row=lpr,
+                     epoch_flags=ef)
     Lv, Mv = t(w.L.vals, dtype), t(w.M.vals, dtype)
     xs = torch.empty((w.n, k), device="cuda", dtype=dtype)
     sch.execute(Lv, Mv, b=t(w.b, dtype), x_save=xs)
@@ -35,14 +36,17 @@ def test_adjoint_trsv_spmv(dtype, k, lpr):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("k", [1, 16])
-@pytest.mark.parametrize("lpr", [0, 16, 32])
-def test_adjoint_spmv_trsv(dtype, k, lpr):
+@pytest.mark.parametrize("k,ef", [(1, False), (1, True), (16, False)])
+@pytest.mark.parametrize("lpr", [0, 1, 16, 32])
+def test_adjoint_spmv_trsv(dtype, k, ef, lpr):
     need_cuda()
     w = I.spmv_trsv_powerlaw(n=12000, k=k, mean=16, lmax=300, halfband=700, seed=43)
     z_ref = oracle.spmv_trsv(w.M, w.L, w.x_in, w.b)
     gb_ref, gx_ref, gL_ref, gA_ref = oracle.adj_spmv_trsv(w.M, w.L, w.x_in, z_ref, w.gy)
-    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, lanes_per_row=lpr)
+    if lpr and lpr < k:
+        pytest.skip("lanes per row below the RHS tile is raised to the tile")
+    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, lanes_per_row=lpr,
+                     epoch_flags=ef)
     Lv, Av, xin = t(w.L.vals, dtype), t(w.M.vals, dtype), t(w.x_in, dtype)
     z = sch.execute(Lv, Av, b=t(w.b, dtype), x_in=xin)
     gx, gL, gA = torch.empty_like(xin), torch.empty_like(Lv), torch.empty_like(Av)

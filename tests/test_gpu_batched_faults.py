@@ -64,7 +64,8 @@ def test_batched_matches_single_instance_bitwise():
         off += x.n
 
 
-def test_timeout_is_reported_not_hung():
+@pytest.mark.parametrize("ef", [False, True])
+def test_timeout_is_reported_not_hung(ef):
     # a chain (bidiagonal L) in one partition run by one warp; swapping its first two items
     # makes that warp wait for a row only it would compute later: a flag nothing sets.
     # The bounded wait (2 ms here) must end the launch with SF_ERR_TIMEOUT.
@@ -73,7 +74,7 @@ def test_timeout_is_reported_not_hung():
     D = np.eye(n) * 2 + np.eye(n, k=-1)
     L = dense_to_csr(D)
     b = np.ones((n, 1))
-    sch = sf.inspect("trsv", dev_csr(L), lanes_per_row=32, part_cost_target=10 ** 9)
+    sch = sf.inspect("trsv", dev_csr(L), lanes_per_row=32, part_cost_target=10 ** 9, epoch_flags=ef)
     assert sch.info()["n_parts"] == 1
     sch.set_timeout(2_000_000)
     sch.debug_swap(0, 1)

@@ -19,13 +19,13 @@ def _lap3d(nx=14, k=1):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("k", [1, 3, 16, 32, 40])
+@pytest.mark.parametrize("k,ef", [(1, False), (1, True), (3, False), (16, False), (32, False), (40, False)])
 @pytest.mark.parametrize("lpr", [0, 1, 4, 32])
-def test_trsv_spmv(dtype, k, lpr):
+def test_trsv_spmv(dtype, k, ef, lpr):
     need_cuda()
     w = _lap3d(11, k)
     x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
-    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr, epoch_flags=ef)
     xs = torch.empty((w.n, k), device="cuda", dtype=dtype)
     y = sch.execute(t(w.L.vals, dtype), t(w.M.vals, dtype), b=t(w.b, dtype), x_save=xs)
     sch.check()
@@ -34,13 +34,13 @@ def test_trsv_spmv(dtype, k, lpr):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("k", [1, 2, 16])
+@pytest.mark.parametrize("k,ef", [(1, False), (1, True), (2, False), (16, False)])
 @pytest.mark.parametrize("lpr", [0, 1, 8, 32])
-def test_spmv_trsv(dtype, k, lpr):
+def test_spmv_trsv(dtype, k, ef, lpr):
     need_cuda()
     w = I.spmv_trsv_powerlaw(n=20000, k=k, mean=16, lmax=400, halfband=900, seed=31)
     z_ref = oracle.spmv_trsv(w.M, w.L, w.x_in, w.b)
-    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr)
+    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr, epoch_flags=ef)
     z = sch.execute(t(w.L.vals, dtype), t(w.M.vals, dtype), b=t(w.b, dtype), x_in=t(w.x_in, dtype))
     sch.check()
     assert col_rel_err(host(z), z_ref) < TOL[dtype]
@@ -78,12 +78,12 @@ def test_ic0_with_intersections_and_alone():
         assert vec_rel_err(host(lf), lf_ref) < 1e-12
 
 
-@pytest.mark.parametrize("k", [1, 5])
-def test_trsv_alone_and_unfused_path(k):
+@pytest.mark.parametrize("k,ef", [(1, False), (1, True), (5, False)])
+def test_trsv_alone_and_unfused_path(k, ef):
     need_cuda()
     w = _lap3d(10, k)
     x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
-    st = sf.inspect("trsv", dev_csr(w.L))
+    st = sf.inspect("trsv", dev_csr(w.L), epoch_flags=ef)
     x = st.execute(t(w.L.vals), b=t(w.b))
     y = sf.spmv(dev_csr(w.M), t(w.M.vals), x)
     st.check()
@@ -110,8 +110,8 @@ def test_integer_exact_bitwise():
     M = I.Csr(n, n, Mp.rowptr, Mp.colidx, np.round(Mp.vals * 4))
     x_ref, y_ref = oracle.trsv_spmv(L, M, b)
     assert np.array_equal(x_ref, x_int)
-    for lpr in (1, 4, 32):
-        sch = sf.inspect("trsv_spmv", dev_csr(L), dev_csr(M), lanes_per_row=lpr)
+    for lpr, ef in ((1, False), (4, False), (32, False), (4, True)):
+        sch = sf.inspect("trsv_spmv", dev_csr(L), dev_csr(M), lanes_per_row=lpr, epoch_flags=ef)
         xs = torch.empty((n, 1), device="cuda", dtype=torch.float64)
         y = sch.execute(t(L.vals), t(M.vals), b=t(b), x_save=xs)
         sch.check()
@@ -154,12 +154,14 @@ def test_edge_cases_tiny_and_diagonal():
         assert col_rel_err(host(x), oracle.trsv_lower(Ld, bd)) < 1e-12
 
 
-def test_repeated_launches_and_epochs():
-    # many launches of one schedule: flags are never cleared, the epoch advances
+@pytest.mark.parametrize("ef", [False, True])
+def test_repeated_launches_and_epochs(ef):
+    # many launches of one schedule: flags are never cleared, the epoch advances; value
+    # flags are reset by the launch itself
     need_cuda()
     w = _lap3d(9, 1)
     _, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
-    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M))
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), epoch_flags=ef)
     Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
     y = torch.empty_like(b)
     for _ in range(50):
@@ -173,14 +175,48 @@ def test_repeated_launches_and_epochs():
     assert col_rel_err(host(y3), np.repeat(y_ref, 3, axis=1)) < 1e-12
 
 
-def test_cuda_graph_replay():
+@pytest.mark.parametrize("ef", [False, True])
+def test_cuda_graph_replay(ef):
     need_cuda()
     w = _lap3d(10, 1)
     _, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
-    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M))
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), epoch_flags=ef)
     g = sf.GraphedExecute(sch, L_vals=t(w.L.vals), M_vals=t(w.M.vals), b=t(w.b), y=torch.empty((w.n, 1), device="cuda",
                                                                                              dtype=torch.float64))
     for _ in range(5):
         out = g.replay()
     sch.check()
     assert col_rel_err(host(out), y_ref) < 1e-12
+
+
+@pytest.mark.parametrize("bps", [1, 2])
+def test_grid_limits_and_set_launch(bps):
+    # fewer resident blocks and launch-shape changes after inspection keep results exact
+    need_cuda()
+    w = _lap3d(12, 1)
+    _, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), blocks_per_sm=bps)
+    Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
+    for lpr, ef in ((1, 0), (8, 1), (32, 0)):
+        sch.set_launch(lanes_per_row=lpr, epoch_flags=ef)
+        y = sch.execute(Lv, Mv, b=b)
+        sch.check()
+        assert col_rel_err(host(y), y_ref) < 1e-12
+    assert sch.info()["blocks_per_sm"] == bps
+
+
+@pytest.mark.parametrize("pair", ["trsv_spmv", "spmv_trsv"])
+@pytest.mark.parametrize("lpr", [1, 4])
+def test_dynamic_ticket_queue(pair, lpr):
+    need_cuda()
+    if pair == "trsv_spmv":
+        w = _lap3d(12, 1)
+        ref = oracle.trsv_spmv(w.L, w.M, w.b)[1]
+    else:
+        w = I.spmv_trsv_powerlaw(n=20000, k=1, mean=16, lmax=400, halfband=900, seed=31)
+        ref = oracle.spmv_trsv(w.M, w.L, w.x_in, w.b)
+    sch = sf.inspect(pair, dev_csr(w.L), dev_csr(w.M), lanes_per_row=lpr, dynamic_queue=True)
+    assert sch.info()["dynamic_queue"] == 1
+    y = sch.execute(t(w.L.vals), t(w.M.vals), b=t(w.b), x_in=t(w.x_in) if w.x_in is not None else None)
+    sch.check()
+    assert col_rel_err(host(y), ref) < 1e-12

@@ -86,6 +86,8 @@ double reuse_ratio(sf_pair pair, long long n, long long sl, long long sm) {
 
 }  // namespace
 
+void sf::set_error_detail(const char *msg) { snprintf(g_detail, sizeof g_detail, "%s", msg); }
+
 struct sf_schedule {
     sf_pair pair = SF_TRSV;
     int n = 0;

@@ -54,6 +54,10 @@ enum PatCode : unsigned {
     PAT_ROWPTR0 = 1, PAT_NNZ = 2, PAT_ROWPTR = 3, PAT_COL_RANGE = 4, PAT_UNSORTED = 5, PAT_DIAG = 6
 };
 
+// Pattern check kernel: minimises (code << 32 | row) of the first violation into *status.
+__global__ void k_check_csr(int n_rows, int n_cols, long long nnz, const int *__restrict__ rp,
+                            const int *__restrict__ ci, int lower, unsigned long long *status);
+
 int bits_for(unsigned long long maxval);
 template <typename T>
 cudaError_t scan_excl(const T *in, T *out, long long n, cudaStream_t s, Arena &ar);

@@ -71,6 +71,8 @@ cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int blocks, c
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf);
 int occupancy_adj(int mode, int dtype, int lpr, bool vf);
+// Sets the thread-local text returned by sf_last_error_detail.
+void set_error_detail(const char *msg);
 cudaError_t launch_spmv(int dtype, int lpr, int kt, int nrows, int k, const int *rp, const int *ci,
                         const void *v, const void *x, const void *b, void *y, cudaStream_t s);
 

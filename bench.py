@@ -319,8 +319,12 @@ def run_gpu(args):
     from paper_2111_12238_gb300 import sparsefusion as sf  # noqa: F401
 
     wl = make_workload(args.workload, args.dtype)
+    kt = 1
+    while kt < wl["k"] and kt < 32:
+        kt *= 2
     launch_opts = dict(lanes_per_row=args.lanes, blocks_per_sm=args.blocks_per_sm, epoch_flags=args.epoch_flags,
-                       part_cost_target=args.part_cost, dynamic_queue=args.dynamic_queue)
+                       part_cost_target=args.part_cost, dynamic_queue=args.dynamic_queue,
+                       rhs_tile=kt if wl["k"] > 1 else 0)
     g = Gpu(wl, args.dtype, device, launch_opts)
     fns = [g.fwd] + ([g.adj] if wl["adj"] else [])
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device) if wl["fits_l2"] else None
@@ -330,6 +334,18 @@ def run_gpu(args):
             f()
         g.unfused()
     g.check()
+    tuned = {}
+    if not args.no_tune:
+        # the project's autotuner picks lanes per row and partition size for each pass,
+        # the unfused comparison path included
+        from paper_2111_12238_gb300 import autotune
+        kw = dict(dtype=g.dt, k=wl["k"], budget_s=args.tune_seconds, use_cache=False)
+        tuned["fwd"] = autotune.tune(g.sched, g.fwd, which=0, **kw)
+        if wl["adj"]:
+            tuned["adj"] = autotune.tune(g.sched, g.adj, which=1, **kw)
+        tuned["unfused"] = autotune.tune(g.un_sched, g.unfused, which=0, **kw)
+        for v in tuned.values():
+            v.pop("trials", None)
     if args.steps is None:
         # size the timed region to about 3 s of device time
         one, _ = _time_loop(torch, fns, 3, flush)
@@ -428,7 +444,8 @@ def run_gpu(args):
             "instances": len(wl["w"].instances) or 1,
         },
         "roofline": {
-            "kernel": f"k_exec ({dom})",
+            "kernel": "fused forward k_exec (one launch)" if dom == "fwd" else
+                      "sf_adjoint (value gathers, fused k_exec pass, gradient passes)",
             "bound": "hbm",
             "achieved": achieved,
             "peak": hbm,
@@ -453,9 +470,12 @@ def run_gpu(args):
         "inspect_ms": g.inspect_s * 1e3,
         "ner_vs_unfused": (g.inspect_s * 1e3 / (un_ms - fwd_ms)) if un_ms > fwd_ms else None,
         "lanes_per_row": info["lanes_per_row"], "n_parts": info["n_parts"],
+        "tuned": tuned,
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": len(fns) * args.steps,
+        # one fused launch per forward; per adjoint two value gathers, the fused pass and up to
+        # two gradient passes
+        "gpu_launches": args.steps * (1 + (5 if wl["adj"] else 0)),
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -543,6 +563,8 @@ def main():
     ap.add_argument("--part-cost", type=int, default=0, help="partition cost target (0 = auto)")
     ap.add_argument("--epoch-flags", action="store_true", help="publish through epoch flags even for k = 1")
     ap.add_argument("--dynamic-queue", action="store_true", help="draw partitions from a ticket counter")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the default launch shape)")
+    ap.add_argument("--tune-seconds", type=float, default=8.0, help="time budget of each autotuning search")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = args.steps if args.steps is not None else 20

@@ -147,6 +147,9 @@ sf_status sf_execute(const sf_schedule *sch, sf_dtype dt, int32_t k, const void 
  *  SF_SPMV_TRSV (z = L^-1 (b - A x_in)): saved = z, gy = dL/dz. Computes lam = L^-T gz;
  *    writes gb = lam, and when non-NULL gx_in = -A^T lam, gL_vals with gL_ij =
  *    -sum_c lam_ic z_jc, gM_vals (pattern of A) with gA_ij = -sum_c lam_ic x_in_jc.
+ * Launches: the values of L^T and M^T (A^T) are first gathered into transposed order in
+ * library-owned buffers, then the fused pass runs on the transposed schedule, then the value
+ * gradients are written by a streaming pass over the rows of L and M (A).
  * Other pairs return SF_ERR_UNSUPPORTED. Same stream and ownership rules as sf_execute. */
 sf_status sf_adjoint(const sf_schedule *sch, sf_dtype dt, int32_t k, const void *L_vals,
                      const void *M_vals, const void *x_in, const void *saved, const void *gy,
@@ -190,6 +193,10 @@ typedef struct {
     int32_t dynamic_queue;             /* 1 when SF_DYNAMIC_QUEUE is in effect */
     double reuse_ratio;                /* Table 2 / §2.2 reuse ratio of the pair */
     double inspect_ms;                 /* wall time of the inspector call */
+    int64_t wide_cost, adj_wide_cost;  /* vertices of cost above this run on a whole warp in a
+                                          partition of their own (0: none) */
+    int64_t cost_total, adj_cost_total; /* sum of the vertex costs c(v) of each schedule */
+    int32_t adj_lanes_per_row, reserved2;
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -200,12 +207,20 @@ sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 sf_status sf_schedule_export(const sf_schedule *sch, int32_t which, int32_t *level,
                              int32_t *order, int32_t *part_ptr);
 
-/* Changes launch parameters without re-inspecting: lanes_per_row (1..32, pow2), rhs_tile
+/* Changes launch parameters of both directions without re-inspecting (the partition cut
+ * stays as it was; see sf_schedule_recut): lanes_per_row (1..32, pow2), rhs_tile
  * (1..lanes_per_row, pow2) and blocks_per_sm (>= 1); 0 keeps the current value.
  * epoch_flags: 1 always publishes through epoch flags, 0 uses value flags when k = 1,
  * -1 keeps the current setting. */
 sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_t rhs_tile,
                                  int32_t blocks_per_sm, int32_t epoch_flags);
+
+/* Re-cuts the partitions (§3.1 coarsening) of the forward (which = 0), adjoint (1) or both
+ * (-1) schedules for a new cost target (0 = automatic) and, when lanes_per_row != 0, a new
+ * lane count; levels and order are kept. Synchronises `stream` before and after; no launch
+ * of this schedule may be pending on another stream. Used by autotuning. */
+sf_status sf_schedule_recut(sf_schedule *sch, int32_t which, int64_t part_cost_target,
+                            int32_t lanes_per_row, void *stream);
 
 /* Sets the time limit of one dependence wait (0 = 2 s). */
 sf_status sf_schedule_set_timeout(sf_schedule *sch, uint64_t timeout_ns);

@@ -293,13 +293,14 @@ def order(level, n):
     return o, depth
 
 
-def partition(order_, n, cost, target):
+def partition(order_, n, cost, target, wide=0):
+    """Partition pointers of the cut (items of cost > wide, if wide > 0, stand alone)."""
     lib = _load()
     o, po = _i32(order_)
     c = np.ascontiguousarray(cost, dtype=np.int64)
     pp, ppp = _out(len(o) + 1, np.int32)
     P = lib.orc_partition(C.c_int64(len(o)), C.c_int32(n), po, c.ctypes.data_as(C.c_void_p),
-                          C.c_int64(int(target)), ppp)
+                          C.c_int64(int(target)), C.c_int64(int(wide)), ppp)
     return pp[: P + 1].copy()
 
 
@@ -317,13 +318,13 @@ def validate(kind, L, M, order_, part_ptr):
                             ppp, C.c_int64(len(pp) - 1))
 
 
-def schedule(kind, what, L, M, target):
+def schedule(kind, what, L, M, target, wide=0):
     """Levels, order and partition pointers of one schedule, as the inspector must build
     them: returns dict(level, order, part_ptr, depth, cost)."""
     lev = levels(kind, L, M)
     o, depth = order(lev, L.n_rows)
     c = costs(what, L, M)
-    pp = partition(o, L.n_rows, c, target)
+    pp = partition(o, L.n_rows, c, target, wide)
     return dict(level=lev, order=o, part_ptr=pp, depth=depth, cost=c)
 
 

@@ -292,8 +292,9 @@ int orc_levels(int32_t kind, int32_t n, const int32_t *lrp, const int32_t *lci,
  *   PAIRED (SpIC0->SpTRSV, kernel 4): 2 nnz(L_i) + sum_{j in L_i, j<i} nnz(L_j) + 1
  *   PAIRED (SpTRSV alone, kernel 5): nnz(L_i) + 1
  *   PAIRED (SpIC0 alone, kernel 6): nnz(L_i) + sum_{j in L_i, j<i} nnz(L_j) + 1
- *   PAIRED_T (kernel 2): nnz(M^T_j) + nnz(L^T_j) + nnz(L_j) + nnz(M_j) + 1
- *   SEP_T  tag 0: nnz(L^T_j) + nnz(L_j) + nnz(A_j) + 1      tag 1: nnz(A^T_j) + 1
+ *   PAIRED_T (kernel 2): nnz(M^T_j) + nnz(L^T_j) + 1
+ *   SEP_T  tag 0: nnz(L^T_j) + 1      tag 1: nnz(A^T_j) + 1
+ * (the adjoint's value gradients are a separate streaming pass, not part of these items)
  * `what` selects the formula: 0 SEP, 1 PAIRED_T, 2 SEP_T, 3 SpMV->SpTRSV,
  * 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0. Output cost[v] for every vertex. */
 int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, const int32_t *mrp,
@@ -315,8 +316,8 @@ int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, c
                 if (lci[e] < i) s += lrp[lci[e] + 1] - lrp[lci[e]];
         switch (what) {
             case 0: cost[i] = nl + 1; cost[n + i] = nm + 1; break;
-            case 1: cost[i] = colM[i] + colL[i] + nl + nm + 1; break;
-            case 2: cost[i] = colL[i] + nl + nm + 1; cost[n + i] = colM[i] + 1; break;
+            case 1: cost[i] = colM[i] + colL[i] + 1; break;
+            case 2: cost[i] = colL[i] + 1; cost[n + i] = colM[i] + 1; break;
             case 3: cost[i] = nm + nl + 1; break;
             case 4: cost[i] = 2 * nl + s + 1; break;
             case 5: cost[i] = nl + 1; break;
@@ -348,19 +349,23 @@ int orc_order(int64_t nv, int32_t n, const int32_t *level, int32_t *order) {
     return depth;
 }
 
-/* Partition cut of the linearised order (coarsening of consecutive wavefronts, §3.2.1,
+/* Partition cut of the linearised order (coarsening of consecutive wavefronts, §3.1,
  * into contiguous work items): with S_q the exclusive prefix sum of c(order[q]), item q
  * belongs to partition floor(S_q / C); partitions are the maximal runs of equal quotient.
+ * An item whose cost exceeds W (W > 0) is "wide" and sits in a partition of its own.
  * Writes part_ptr[0..P] and returns P. */
 int64_t orc_partition(int64_t nv, int32_t n, const int32_t *order, const int64_t *cost,
-                      int64_t C, int32_t *part_ptr) {
+                      int64_t C, int64_t W, int32_t *part_ptr) {
     int64_t S = 0, P = 0, prev = -1;
+    int prev_wide = 0;
     for (int64_t q = 0; q < nv; ++q) {
         uint32_t o = (uint32_t)order[q];
         int64_t v = (int64_t)(o >> 31) * n + (o & 0x7fffffffu);
         int64_t p = S / C;
-        if (q == 0 || p != prev) part_ptr[P++] = (int32_t)q;
+        int wide = W > 0 && cost[v] > W;
+        if (q == 0 || p != prev || wide || prev_wide) part_ptr[P++] = (int32_t)q;
         prev = p;
+        prev_wide = wide;
         S += cost[v];
     }
     part_ptr[P] = (int32_t)nv;

@@ -61,6 +61,11 @@ struct Dir {
     int *level = nullptr;
     int *order = nullptr;
     int *part_ptr = nullptr;
+    unsigned char *part_wide = nullptr;
+    long long W = 0;            // items of cost > W run on a whole warp (0: none)
+    int lpr = 1;                // lanes per row of this direction's launches
+    int *cost = nullptr;        // c(v) of every vertex (kept for re-cutting)
+    long long cost_total = 0;
     unsigned *flags = nullptr;
     ExecState *st = nullptr;
 };
@@ -97,6 +102,7 @@ struct sf_schedule {
     bool hasM = false;
     DevCsrT LT, MT;
     bool hasLT = false, hasMT = false;
+    void *LTv = nullptr, *MTv = nullptr;   // adjoint: values in transposed order (8 B per entry)
     Dir fwd, adj;
     int lpr = 4, kt = 0;
     int blocks_per_sm = 0;
@@ -156,19 +162,45 @@ sf_status copy_pattern(sf_schedule *S, const sf_csr *src, DevCsr &dst, cudaStrea
     return SF_OK;
 }
 
+// Cost prefix and partition cut of one direction (the part of the inspection that the
+// launch shape influences): C_user > 0 is the cost target, else about max(1, G/4) items
+// per partition with G = 32 / lanes the groups of a warp.
+sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Arena &tmp) {
+    const long long nv = d.nv;
+    long long *cs = (long long *)tmp.alloc(sizeof(long long) * nv);
+    long long *Sx = (long long *)tmp.alloc(sizeof(long long) * (nv + 1));
+    if (!cs || !Sx) return fail(SF_ERR_OOM, "inspector: out of device memory");
+    long long total = 0;
+    cudaError_t e = prefix_costs(nv, S->n, d.order, d.cost, cs, Sx, &total, s, tmp);
+    if (e != cudaSuccess) return from_cuda(e, "cost prefix");
+    d.cost_total = total;
+    long long C = C_user;
+    if (C <= 0) {
+        const long long mean = std::max<long long>(1, (total + nv - 1) / nv);
+        C = (long long)std::max(1, (32 / d.lpr) / 4) * mean;
+    }
+    d.C = C;
+    // rows much longer than a group's lanes can cover quickly get the whole warp
+    d.W = d.lpr < 32 ? 16LL * d.lpr + 1 : 0;
+    e = cut_partitions(nv, Sx, cs, C, d.W, d.part_ptr, d.part_wide, &d.n_parts, s, tmp);
+    if (e != cudaSuccess) return from_cuda(e, "partition cut");
+    return SF_OK;
+}
+
 sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user, cudaStream_t s, Arena &tmp) {
     const int n = S->n;
     d.kind = kind;
+    d.lpr = S->lpr;
     d.nv = (kind == K_SEP || kind == K_SEP_T) ? 2LL * n : (long long)n;
     const long long nv = d.nv;
     d.level = (int *)S->keep.alloc(sizeof(int) * nv);
     d.order = (int *)S->keep.alloc(sizeof(int) * nv);
     d.part_ptr = (int *)S->keep.alloc(sizeof(int) * (nv + 1));
+    d.part_wide = (unsigned char *)S->keep.alloc((size_t)nv + 1);
     d.flags = (unsigned *)S->keep.alloc(sizeof(unsigned) * (size_t)n);
     d.st = (ExecState *)S->keep.alloc(sizeof(ExecState));
-    int *cost = (int *)tmp.alloc(sizeof(int) * nv);
-    long long *Sx = (long long *)tmp.alloc(sizeof(long long) * (nv + 1));
-    if (!d.level || !d.order || !d.part_ptr || !d.flags || !d.st || !cost || !Sx)
+    d.cost = (int *)S->keep.alloc(sizeof(int) * nv);
+    if (!d.level || !d.order || !d.part_ptr || !d.part_wide || !d.flags || !d.st || !d.cost)
         return fail(SF_ERR_OOM, "inspector: out of device memory");
     SF_CK(cudaMemsetAsync(d.flags, 0, sizeof(unsigned) * (size_t)n, s), "inspector");
     SF_CK(cudaMemcpyAsync(d.st, &kInitState, sizeof(ExecState), cudaMemcpyHostToDevice, s), "inspector");
@@ -199,21 +231,10 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     e = build_order(nv, n, d.level, d.depth, d.order, s, tmp);
     if (e != cudaSuccess) return from_cuda(e, "ordering");
     e = vertex_costs(what, n, S->L, S->hasM ? &S->M : nullptr, S->hasLT ? &S->LT : nullptr,
-                     S->hasMT ? &S->MT : nullptr, cost, s);
+                     S->hasMT ? &S->MT : nullptr, d.cost, s);
     if (e != cudaSuccess) return from_cuda(e, "vertex costs");
-    long long total = 0;
-    e = prefix_costs(nv, n, d.order, cost, Sx, &total, s, tmp);
-    if (e != cudaSuccess) return from_cuda(e, "cost prefix");
-    long long C = C_user;
-    if (C <= 0) {
-        // a partition of about max(1, G/4) items, G = 32 / lanes the groups of a warp: small
-        // enough that a late item delays few others, large enough to keep groups busy
-        const long long mean = std::max<long long>(1, (total + nv - 1) / nv);
-        C = (long long)std::max(1, (32 / S->lpr) / 4) * mean;
-    }
-    d.C = C;
-    e = cut_partitions(nv, Sx, C, d.part_ptr, &d.n_parts, s, tmp);
-    if (e != cudaSuccess) return from_cuda(e, "partition cut");
+    sf_status st = cut_dir(S, d, C_user, s, tmp);
+    if (st != SF_OK) return st;
     d.present = true;
     return SF_OK;
 }
@@ -263,6 +284,9 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
         if (S->pair == SF_TRSV_SPMV) st = build_dir(S, S->adj, K_PAIRED_T, 1, o.part_cost_target, s, tmp);
         else st = build_dir(S, S->adj, K_SEP_T, 2, o.part_cost_target, s, tmp);
         if (st != SF_OK) return st;
+        S->LTv = S->keep.alloc(8 * (size_t)std::max<long long>(S->L.nnz, 1));
+        S->MTv = S->keep.alloc(8 * (size_t)std::max<long long>(S->M.nnz, 1));
+        if (!S->LTv || !S->MTv) return fail(SF_ERR_OOM, "inspector: out of device memory");
     }
     S->reuse = reuse_ratio(S->pair, S->n, S->L.nnz, S->hasM ? S->M.nnz : 0);
     SF_CK(cudaStreamSynchronize(s), "inspector");
@@ -349,9 +373,12 @@ void *value_flag_buffer(int mode, const ExecArgs &a) {
 
 sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int k, ExecArgs &a, cudaStream_t s) {
     const int kt = S->kt ? std::min(S->kt, 32) : std::min(pow2_ceil(k), 32);
-    const int lpr = std::max(S->lpr, kt);
+    const int lpr = std::max(d.lpr, kt);
     a.order = d.order;
     a.part_ptr = d.part_ptr;
+    a.part_wide = d.part_wide;
+    a.LTv = S->LTv;
+    a.MTv = S->MTv;
     a.n_parts = d.n_parts;
     a.n = S->n;
     a.k = k;
@@ -560,7 +587,31 @@ SF_API sf_status sf_adjoint(const sf_schedule *S, sf_dtype dt, int32_t k, const 
         if (gM_vals && !x_in) return fail(SF_ERR_INVALID_ARG, "gM_vals (gradient of A) needs x_in");
         mode = M_ADJ_SPMV_TRSV;
     }
-    return launch(S, S->adj, mode, dt, k, a, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dtype = dt == SF_F64 ? 0 : 1;
+    // 1. values of L^T and M^T (A^T) in transposed order, one coalesced gather each
+    SF_CK(launch_gather_vals(dtype, S->L.nnz, S->LT.perm, L_vals, S->LTv, s), "adjoint gather");
+    SF_CK(launch_gather_vals(dtype, S->M.nnz, S->MT.perm, M_vals, S->MTv, s), "adjoint gather");
+    // 2. the fused pass on the transposed schedule
+    sf_status st = launch(S, S->adj, mode, dt, k, a, s);
+    if (st != SF_OK) return st;
+    // 3. value gradients restricted to the patterns, streamed row by row
+    if (S->pair == SF_TRSV_SPMV) {
+        if (gL_vals)   // gL_ij = -sum_c lam_ic x_jc
+            SF_CK(launch_grad_rows(dtype, S->n, S->L.nnz, k, S->L.rowptr, S->L.colidx, gb, saved, -1.0, gL_vals, s),
+                  "adjoint gradients");
+        if (gM_vals)   // gM_ij = sum_c gy_ic x_jc
+            SF_CK(launch_grad_rows(dtype, S->n, S->M.nnz, k, S->M.rowptr, S->M.colidx, gy, saved, 1.0, gM_vals, s),
+                  "adjoint gradients");
+    } else {
+        if (gL_vals)   // gL_ij = -sum_c lam_ic z_jc
+            SF_CK(launch_grad_rows(dtype, S->n, S->L.nnz, k, S->L.rowptr, S->L.colidx, gb, saved, -1.0, gL_vals, s),
+                  "adjoint gradients");
+        if (gM_vals)   // gA_ij = -sum_c lam_ic x_in_jc
+            SF_CK(launch_grad_rows(dtype, S->n, S->M.nnz, k, S->M.rowptr, S->M.colidx, gb, x_in, -1.0, gM_vals, s),
+                  "adjoint gradients");
+    }
+    return SF_OK;
 }
 
 SF_API sf_status sf_spmv(sf_dtype dt, int32_t k, const sf_csr *M, const void *M_vals, const void *x, const void *b,
@@ -682,11 +733,16 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
         info->adj_n_items = S->adj.nv;
         info->adj_part_cost_target = S->adj.C;
     }
-    info->lanes_per_row = S->lpr;
+    info->lanes_per_row = S->fwd.lpr;
+    info->adj_lanes_per_row = S->adj.lpr;
     info->rhs_tile = S->kt;
     info->part_cost_target = S->fwd.C;
     info->packing = S->packing;
     info->blocks_per_sm = S->blocks_per_sm;
+    info->wide_cost = S->fwd.W;
+    info->adj_wide_cost = S->adj.W;
+    info->cost_total = S->fwd.cost_total;
+    info->adj_cost_total = S->adj.cost_total;
     info->epoch_flags = S->epoch_flags ? 1 : 0;
     info->dynamic_queue = S->dynamic_queue ? 1 : 0;
     info->reuse_ratio = S->reuse;
@@ -717,9 +773,32 @@ SF_API sf_status sf_schedule_set_launch(sf_schedule *S, int32_t lanes_per_row, i
     const int kt = rhs_tile ? rhs_tile : S->kt;
     if (kt > lpr) return fail(SF_ERR_INVALID_ARG, "rhs_tile must not exceed lanes_per_row");
     S->lpr = lpr;
+    S->fwd.lpr = lpr;
+    S->adj.lpr = lpr;
     S->kt = kt;
     if (blocks_per_sm) S->blocks_per_sm = blocks_per_sm;
     if (epoch_flags >= 0) S->epoch_flags = epoch_flags == 1;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_recut(sf_schedule *S, int32_t which, int64_t part_cost_target, int32_t lanes_per_row,
+                                   void *stream) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (part_cost_target < 0) return fail(SF_ERR_INVALID_ARG, "part_cost_target must be >= 0");
+    if (lanes_per_row && !is_pow2_upto32(lanes_per_row)) return fail(SF_ERR_INVALID_ARG, "bad lanes_per_row");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    cudaStream_t s = (cudaStream_t)stream;
+    SF_CK(cudaStreamSynchronize(s), "recut");      // no launch of this schedule may be in flight
+    Arena tmp;
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w) {
+        if ((which != -1 && which != w) || !dirs[w]->present) continue;
+        if (lanes_per_row) dirs[w]->lpr = std::max(lanes_per_row, S->kt);
+        sf_status st = cut_dir(S, *dirs[w], part_cost_target, s, tmp);
+        if (st != SF_OK) return st;
+    }
+    SF_CK(cudaStreamSynchronize(s), "recut");
     return SF_OK;
 }
 

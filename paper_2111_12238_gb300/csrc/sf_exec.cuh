@@ -386,87 +386,55 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
 
 // Adjoint of SpTRSV -> SpMV as a paired pass on the transposed schedule (item j = column
 // j of L): u_j = (M^T gy)_j needs no wait; lam_j = (u_j - sum_{i>j} L_ij lam_i) / L_jj
-// waits for lam_i; gb = lam. After publishing, the row's gradients:
-// gL_j* = -lam_j x_*, gM_j* = gy_j x_*.
+// waits for lam_i; gb = lam. Values of M^T and L^T come in transposed order (a.MTv, a.LTv);
+// the value gradients run afterwards as a separate streaming pass.
 template <typename T, int LPR, bool VF>
 __device__ bool item_adj_trsv_spmv(const ExecArgs &a, int j, unsigned epoch, int gl, int gbase, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ms = __ldg(a.MTrp + j), me = __ldg(a.MTrp + j + 1);
     const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);   // first entry of L^T row j is L_jj
-    const T *Lv = (const T *)a.Lv, *gy = (const T *)a.gy, *x = (const T *)a.saved;
+    const T *LTv = (const T *)a.LTv, *gy = (const T *)a.gy;
     T *lam = (T *)a.gb;
-    const T d = __ldg(Lv + __ldg(a.LTperm + ls));
+    const T d = __ldg(LTv + ls);
     if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, j);
     bool ok = true;
-    T lam0 = T(0);
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T u = row_dot<T, D_NONE, true>(a.MTci, a.MTperm, (const T *)a.Mv, ms + s, me, S, gy, k, c, act, a.flags,
-                                       epoch, a.st, a.timeout_ns, j, ok);
-        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, true>(a.LTci, a.LTperm, Lv, ls + 1 + s, le, S, lam, k, c, act,
-                                                         a.flags, epoch, a.st, a.timeout_ns, j, ok);
+        T u = row_dot<T, D_NONE, false>(a.MTci, nullptr, (const T *)a.MTv, ms + s, me, S, gy, k, c, act, a.flags,
+                                        epoch, a.st, a.timeout_ns, j, ok);
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
+                                                          a.flags, epoch, a.st, a.timeout_ns, j, ok);
         u = slice_sum<LPR>(u, kt, gmask);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        const T v = (u - accL) / d;
-        if (c0 == 0) lam0 = v;
-        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, v);
+        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, (u - accL) / d);
     }
     ok = group_ok<LPR>(ok, gmask);
     if (!VF) publish(a, j, epoch, gl, gmask, ok);
-    if (!ok) return false;
-    if (VF) {   // k = 1: lam_j is in every lane's registers (slice sums are group-wide)
-        if (a.gL) grad_row<T, LPR>(a.Lci, __ldg(a.Lrp + j), __ldg(a.Lrp + j + 1), [&](int) { return lam0; }, x, k, kt,
-                                   gl, gbase, T(-1), (T *)a.gL);
-    } else {
-        __syncwarp(gmask);
-        const T *lr = lam + (size_t)j * k;
-        if (a.gL) grad_row<T, LPR>(a.Lci, __ldg(a.Lrp + j), __ldg(a.Lrp + j + 1), [&](int c) { return lr[c]; }, x, k,
-                                   kt, gl, gbase, T(-1), (T *)a.gL);
-    }
-    if (a.gM) {
-        const T *gr = gy + (size_t)j * k;
-        grad_row<T, LPR>(a.Mci, __ldg(a.Mrp + j), __ldg(a.Mrp + j + 1), [&](int c) { return __ldg(gr + c); }, x, k,
-                         kt, gl, gbase, T(1), (T *)a.gM);
-    }
-    return true;
+    return ok;
 }
 
-// Adjoint of SpMV -> SpTRSV, tag 0: lam_j = (gz_j - sum_{i>j} L_ij lam_i) / L_jj, gb = lam,
-// then gL_j* = -lam_j z_*, gA_j* = -lam_j x_in_*.
+// Adjoint of SpMV -> SpTRSV, tag 0: lam_j = (gz_j - sum_{i>j} L_ij lam_i) / L_jj, gb = lam.
 template <typename T, int LPR, bool VF>
 __device__ bool item_adj_lam(const ExecArgs &a, int j, unsigned epoch, int gl, int gbase, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);
-    const T *Lv = (const T *)a.Lv, *gz = (const T *)a.gy;
+    const T *LTv = (const T *)a.LTv, *gz = (const T *)a.gy;
     T *lam = (T *)a.gb;
-    const T d = __ldg(Lv + __ldg(a.LTperm + ls));
+    const T d = __ldg(LTv + ls);
     if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, j);
     bool ok = true;
-    T lam0 = T(0);
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, true>(a.LTci, a.LTperm, Lv, ls + 1 + s, le, S, lam, k, c, act,
-                                                         a.flags, epoch, a.st, a.timeout_ns, j, ok);
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
+                                                          a.flags, epoch, a.st, a.timeout_ns, j, ok);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        const T v = act ? (__ldg(gz + (size_t)j * k + c) - accL) / d : T(0);
-        if (c0 == 0) lam0 = v;
-        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, v);
+        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, (__ldg(gz + (size_t)j * k + c) - accL) / d);
     }
     ok = group_ok<LPR>(ok, gmask);
     if (!VF) publish(a, j, epoch, gl, gmask, ok);
-    if (!ok) return false;
-    const T *lr = lam + (size_t)j * k;
-    if (!VF) __syncwarp(gmask);
-    auto coef = [&](int c) { return VF ? lam0 : lr[c]; };
-    if (a.gL)
-        grad_row<T, LPR>(a.Lci, __ldg(a.Lrp + j), __ldg(a.Lrp + j + 1), coef, (const T *)a.saved, k, kt, gl, gbase,
-                         T(-1), (T *)a.gL);
-    if (a.gM)
-        grad_row<T, LPR>(a.Mci, __ldg(a.Mrp + j), __ldg(a.Mrp + j + 1), coef, (const T *)a.xin, k, kt, gl, gbase,
-                         T(-1), (T *)a.gM);
-    return true;
+    return ok;
 }
 
 // Adjoint of SpMV -> SpTRSV, tag 1: gx_j = -sum_i A_ij lam_i, waiting for each lam_i.
@@ -479,9 +447,9 @@ __device__ bool item_adj_gx(const ExecArgs &a, int j, unsigned epoch, int gl, un
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, true>(a.MTci, a.MTperm, (const T *)a.Mv, ms + s, me, S,
-                                                        (const T *)a.gb, k, c, act, a.flags, epoch, a.st,
-                                                        a.timeout_ns, j, ok);
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.MTci, nullptr, (const T *)a.MTv, ms + s, me, S,
+                                                         (const T *)a.gb, k, c, act, a.flags, epoch, a.st,
+                                                         a.timeout_ns, j, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
         if (s == 0 && act) gx[(size_t)j * k + c] = -acc;
     }
@@ -542,9 +510,16 @@ __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecArgs a) {
     while (p < a.n_parts) {
         const int pn_lane0 = a.dynamic ? draw_ticket(a, lane) : 0;
         const int q0 = __ldg(a.part_ptr + p), q1 = __ldg(a.part_ptr + p + 1);
-        for (int q = q0 + grp; q < q1 && ok; q += G) {
-            const unsigned o = (unsigned)__ldg(a.order + q);
-            ok = run_item<MODE, T, LPR, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
+        if (LPR < 32 && a.part_wide[p]) {
+            // a long row: the whole warp runs it (the cut gives it a partition of its own)
+            const unsigned o = (unsigned)__ldg(a.order + q0);
+            if (ok) ok = run_item<MODE, T, 32, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, lane, 0,
+                                                   0xffffffffu);
+        } else {
+            for (int q = q0 + grp; q < q1 && ok; q += G) {
+                const unsigned o = (unsigned)__ldg(a.order + q);
+                ok = run_item<MODE, T, LPR, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
+            }
         }
         if (!__all_sync(0xffffffffu, ok)) break;
         if (a.dynamic) p = __shfl_sync(0xffffffffu, pn_lane0, 0);

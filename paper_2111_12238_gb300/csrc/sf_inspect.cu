@@ -5,6 +5,7 @@
 // Building blocks are hand-written: a three-phase exclusive scan, a stable LSD radix sort
 // (8-bit digits, per-block histograms, in-tile ranking with warp match), a count/scan/
 // sort transpose and a cooperative persistent Kahn kernel with a bounded grid barrier.
+#include <algorithm>
 #include <vector>
 
 #include "sf_inspect.cuh"
@@ -366,9 +367,11 @@ __device__ bool grid_barrier(KahnCtl *ctl, unsigned nblocks, unsigned long long 
             st_release_u32(&ctl->bar_gen, gen + 1u);
         } else {
             const unsigned long long t0 = global_ns();
-            unsigned it = 0;
+            unsigned it = 0, ns = 32;
             while (ld_acquire_u32(&ctl->bar_gen) == gen) {
-                if ((++it & 255u) == 0u && global_ns() - t0 > tmo) {
+                __nanosleep(ns);
+                if (ns < 256) ns *= 2;
+                if ((++it & 63u) == 0u && global_ns() - t0 > tmo) {
                     atomicExch(&ctl->err, 1u);
                     ok = false;
                     break;
@@ -379,35 +382,60 @@ __device__ bool grid_barrier(KahnCtl *ctl, unsigned nblocks, unsigned long long 
     return __syncthreads_and(ok) != 0;
 }
 
+// Decrements the in-degree of successor t (for 0 <= t) and appends it to the next frontier
+// when it reaches zero; the appends of a warp share one atomic on the frontier counter.
+__device__ __forceinline__ void kahn_visit(int t, int *__restrict__ indeg, int *__restrict__ queue, long long fe,
+                                           unsigned *cnt) {
+    const bool ready = t >= 0 && atomicSub(&indeg[t], 1) == 1;
+    const unsigned m = __ballot_sync(0xffffffffu, ready);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (ready) queue[fe + base + __popc(m & lanemask_lt())] = t;
+}
+
 // Frontier peeling: round r owns the vertices whose last predecessor was removed in
 // round r-1 (its level is r); removing a vertex decrements its successors' in-degrees and
-// appends those that reach zero to the next frontier. Counters of the next frontier are
-// triple-buffered so that no block reads a count while another resets it.
+// appends those that reach zero to the next frontier. One warp expands one frontier vertex
+// (its lanes split the successor list, so long rows do not serialise on one thread).
+// Counters of the next frontier are triple-buffered so that no block reads a count while
+// another resets it.
 __global__ void __launch_bounds__(256) k_kahn(int n1, const int *__restrict__ s1rp, const int *__restrict__ s1ci,
                                               const int *__restrict__ s2rp, const int *__restrict__ s2ci,
                                               int *__restrict__ indeg, int *__restrict__ queue,
                                               int *__restrict__ level, KahnCtl *ctl, unsigned long long tmo) {
     const unsigned nblocks = gridDim.x;
+    const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const long long gwarp = gtid >> 5;
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
     long long fs = 0, fe = (long long)ld_acquire_u32(&ctl->nsrc);
     int round = 0;
     while (fs < fe) {
         unsigned *cnt = &ctl->cnt[round % 3];
-        for (long long idx = fs + gtid; idx < fe; idx += gstride) {
+        for (long long idx = fs + gwarp; idx < fe; idx += nwarp) {
             const int v = queue[idx];
-            level[v] = round;
+            if (lane == 0) level[v] = round;
             if (v < n1) {
-                for (int e = s1rp[v]; e < s1rp[v + 1]; ++e) {
-                    const int t = s1ci[e];
-                    if (t == v) continue;
-                    if (atomicSub(&indeg[t], 1) == 1) queue[fe + atomicAdd(cnt, 1u)] = t;
-                }
-                if (s2rp)
-                    for (int e = s2rp[v]; e < s2rp[v + 1]; ++e) {
-                        const int t = n1 + s2ci[e];
-                        if (atomicSub(&indeg[t], 1) == 1) queue[fe + atomicAdd(cnt, 1u)] = t;
+                const int a1 = s1rp[v], b1 = s1rp[v + 1];
+                for (int e0 = a1; e0 < b1; e0 += 32) {
+                    const int e = e0 + lane;
+                    int t = -1;
+                    if (e < b1) {
+                        t = s1ci[e];
+                        if (t == v) t = -1;
                     }
+                    kahn_visit(t, indeg, queue, fe, cnt);
+                }
+                if (s2rp) {
+                    const int a2 = s2rp[v], b2 = s2rp[v + 1];
+                    for (int e0 = a2; e0 < b2; e0 += 32) {
+                        const int e = e0 + lane;
+                        kahn_visit(e < b2 ? n1 + s2ci[e] : -1, indeg, queue, fe, cnt);
+                    }
+                }
             }
         }
         if (gtid == 0) ctl->cnt[(round + 1) % 3] = 0u;
@@ -443,7 +471,7 @@ cudaError_t kahn_levels(long long nv, int n1, const int *s1rp, const int *s1ci, 
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     long long want = (nv + 255) / 256;
-    long long blocks = (long long)sms * occ;
+    long long blocks = (long long)sms * std::min(occ, 2);   // fewer arrivals per barrier
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;
     unsigned long long tmo = 5000000000ull;   // 5 s per barrier
@@ -481,7 +509,8 @@ __global__ void k_encode_order(long long nv, int n1, const unsigned *__restrict_
     }
 }
 
-// c(v) of §3.1 (nonzeros touched by the iteration) + 1; formulas per `what`:
+// c(v) of §3.1 (nonzeros touched by the iteration) + 1 (adjoint items exclude the value
+// gradients, which run as a separate streaming pass); formulas per `what`:
 // 0 SEP, 1 PAIRED_T, 2 SEP_T, 3 SpMV->SpTRSV, 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0.
 __global__ void k_costs(int what, int n, const int *__restrict__ Lrp, const int *__restrict__ Lci,
                         const int *__restrict__ Mrp, const int *__restrict__ LTrp, const int *__restrict__ MTrp,
@@ -500,8 +529,8 @@ __global__ void k_costs(int what, int n, const int *__restrict__ Lrp, const int 
         }
     switch (what) {
         case 0: cost[i] = nl + 1; cost[n + i] = nm + 1; break;
-        case 1: cost[i] = cm + cl + nl + nm + 1; break;
-        case 2: cost[i] = cl + nl + nm + 1; cost[n + i] = cm + 1; break;
+        case 1: cost[i] = cm + cl + 1; break;
+        case 2: cost[i] = cl + 1; cost[n + i] = cm + 1; break;
         case 3: cost[i] = nm + nl + 1; break;
         case 4: cost[i] = 2 * nl + sj + 1; break;
         case 5: cost[i] = nl + 1; break;
@@ -517,15 +546,25 @@ __global__ void k_gather_cost(long long nv, int n1, const int *__restrict__ orde
     }
 }
 
-__global__ void k_cut_flags(long long nv, const long long *__restrict__ S, long long C, int *__restrict__ f) {
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x)
-        f[q] = (q == 0 || S[q] / C != S[q - 1] / C) ? 1 : 0;
+// A partition starts where floor(S_q / C) changes, and around every wide item (cost > W,
+// W > 0), which gets a partition of its own.
+__global__ void k_cut_flags(long long nv, const long long *__restrict__ S, const long long *__restrict__ cs,
+                            long long C, long long W, int *__restrict__ f) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
+        const bool wide = W > 0 && cs[q] > W;
+        const bool prev_wide = q > 0 && W > 0 && cs[q - 1] > W;
+        f[q] = (q == 0 || S[q] / C != S[q - 1] / C || wide || prev_wide) ? 1 : 0;
+    }
 }
 
 __global__ void k_cut_scatter(long long nv, const int *__restrict__ f, const int *__restrict__ idx,
-                              int *__restrict__ part_ptr) {
+                              const long long *__restrict__ cs, long long W, int *__restrict__ part_ptr,
+                              unsigned char *__restrict__ part_wide) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
-        if (f[q]) part_ptr[idx[q]] = (int)q;
+        if (f[q]) {
+            part_ptr[idx[q]] = (int)q;
+            part_wide[idx[q]] = (W > 0 && cs[q] > W) ? 1 : 0;
+        }
         if (q == 0) part_ptr[idx[nv]] = (int)nv;
     }
 }
@@ -548,10 +587,8 @@ cudaError_t vertex_costs(int what, int n, const DevCsr &L, const DevCsr *M, cons
     return cudaGetLastError();
 }
 
-cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost, long long *S, long long *total,
-                         cudaStream_t s, Arena &ar) {
-    long long *cs = (long long *)ar.alloc(sizeof(long long) * nv);
-    if (!cs) return cudaErrorMemoryAllocation;
+cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost, long long *cs, long long *S,
+                         long long *total, cudaStream_t s, Arena &ar) {
     k_gather_cost<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, n1, order, cost, cs);
     cudaError_t e = scan_excl<long long>(cs, S, nv, s, ar);
     if (e != cudaSuccess) return e;
@@ -560,15 +597,16 @@ cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost
     return cudaStreamSynchronize(s);
 }
 
-cudaError_t cut_partitions(long long nv, const long long *S, long long C, int *part_ptr_out_capacity_nv1,
-                           int *n_parts, cudaStream_t s, Arena &ar) {
+cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs, long long C, long long W,
+                           int *part_ptr_out_capacity_nv1, unsigned char *part_wide, int *n_parts, cudaStream_t s,
+                           Arena &ar) {
     int *f = (int *)ar.alloc(sizeof(int) * nv);
     int *idx = (int *)ar.alloc(sizeof(int) * (nv + 1));
     if (!f || !idx) return cudaErrorMemoryAllocation;
-    k_cut_flags<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, S, C, f);
+    k_cut_flags<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, S, cs, C, W, f);
     cudaError_t e = scan_excl<int>(f, idx, nv, s, ar);
     if (e != cudaSuccess) return e;
-    k_cut_scatter<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, f, idx, part_ptr_out_capacity_nv1);
+    k_cut_scatter<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, f, idx, cs, W, part_ptr_out_capacity_nv1, part_wide);
     e = cudaMemcpyAsync(n_parts, idx + nv, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(s);

@@ -69,10 +69,10 @@ cudaError_t kahn_levels(long long nv, int n1, const int *s1rp, const int *s1ci, 
 cudaError_t build_order(long long nv, int n1, const int *level, int depth, int *order, cudaStream_t s, Arena &ar);
 cudaError_t vertex_costs(int what, int n, const DevCsr &L, const DevCsr *M, const DevCsrT *LT, const DevCsrT *MT,
                          int *cost, cudaStream_t s);
-cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost, long long *S, long long *total,
-                         cudaStream_t s, Arena &ar);
-cudaError_t cut_partitions(long long nv, const long long *S, long long C, int *part_ptr, int *n_parts,
-                           cudaStream_t s, Arena &ar);
+cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost, long long *cs, long long *S,
+                         long long *total, cudaStream_t s, Arena &ar);
+cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs, long long C, long long W,
+                           int *part_ptr, unsigned char *part_wide, int *n_parts, cudaStream_t s, Arena &ar);
 cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci_out, long long total_nnz,
                             int total_rows, cudaStream_t s, Arena &ar);
 

@@ -47,6 +47,7 @@ struct ExecState {
 struct ExecArgs {
     const int *order;
     const int *part_ptr;
+    const unsigned char *part_wide;    // 1: the partition is one long item run by the whole warp
     int n_parts;
     int n;
     int k;
@@ -60,6 +61,7 @@ struct ExecArgs {
     const int *LTrp, *LTci, *LTperm;    // L^T pattern and entry permutation into L
     const int *MTrp, *MTci, *MTperm;    // M^T / A^T
     const void *Lv, *Mv, *xin, *b, *gy, *saved;
+    const void *LTv, *MTv;              // values of L^T and M^T / A^T in transposed order (adjoint)
     void *y, *xs, *gb, *gx, *gL, *gM;
 };
 
@@ -71,6 +73,11 @@ cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int blocks, c
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf);
 int occupancy_adj(int mode, int dtype, int lpr, bool vf);
+// Adjoint helpers: dst[t] = src[perm[t]] (values in transposed order), and the value
+// gradients out[e] = sign * sum_c coef[i*k+c] * vec[col(e)*k+c] over the rows i of a pattern.
+cudaError_t launch_gather_vals(int dtype, long long nnz, const int *perm, const void *src, void *dst, cudaStream_t s);
+cudaError_t launch_grad_rows(int dtype, int n, long long nnz, int k, const int *rp, const int *ci, const void *coef,
+                             const void *vec, double sign, void *out, cudaStream_t s);
 // Sets the thread-local text returned by sf_last_error_detail.
 void set_error_detail(const char *msg);
 cudaError_t launch_spmv(int dtype, int lpr, int kt, int nrows, int k, const int *rp, const int *ci,

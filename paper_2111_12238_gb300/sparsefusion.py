@@ -46,7 +46,10 @@ class SfInfo(C.Structure):
                 ("part_cost_target", C.c_int64), ("adj_part_cost_target", C.c_int64),
                 ("packing", C.c_int32), ("blocks_per_sm", C.c_int32), ("epoch_flags", C.c_int32),
                 ("dynamic_queue", C.c_int32),
-                ("reuse_ratio", C.c_double), ("inspect_ms", C.c_double)]
+                ("reuse_ratio", C.c_double), ("inspect_ms", C.c_double),
+                ("wide_cost", C.c_int64), ("adj_wide_cost", C.c_int64),
+                ("cost_total", C.c_int64), ("adj_cost_total", C.c_int64),
+                ("adj_lanes_per_row", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -74,6 +77,7 @@ _SIGS = {
     "sf_schedule_export": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "sf_schedule_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "sf_schedule_set_timeout": (C.c_int, [_P, C.c_uint64]),
+    "sf_schedule_recut": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_int32, _P]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
@@ -247,6 +251,11 @@ class Schedule:
         _check(load_library().sf_schedule_set_launch(self.handle, int(lanes_per_row), int(rhs_tile),
                                                      int(blocks_per_sm), int(epoch_flags)),
                "sf_schedule_set_launch")
+
+    def recut(self, which=-1, part_cost_target=0, lanes_per_row=0, stream=None):
+        """Re-cuts the partitions for a new cost target and lane count (levels and order kept)."""
+        _check(load_library().sf_schedule_recut(self.handle, int(which), int(part_cost_target), int(lanes_per_row),
+                                                _stream(stream)), "sf_schedule_recut")
 
     def set_timeout(self, ns: int):
         _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")

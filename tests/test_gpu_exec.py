@@ -220,3 +220,36 @@ def test_dynamic_ticket_queue(pair, lpr):
     y = sch.execute(t(w.L.vals), t(w.M.vals), b=t(w.b), x_in=t(w.x_in) if w.x_in is not None else None)
     sch.check()
     assert col_rel_err(host(y), ref) < 1e-12
+
+
+def test_recut_and_autotune_keep_results_exact():
+    need_cuda()
+    from paper_2111_12238_gb300 import autotune
+    w = _lap3d(12, 1)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    gb_ref, _, _ = oracle.adj_trsv_spmv(w.L, w.M, x_ref, w.gy)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True)
+    Lv, Mv, b, gy = t(w.L.vals), t(w.M.vals), t(w.b), t(w.gy)
+    xs = torch.empty_like(b)
+    p0 = sch.info()["n_parts"]
+    sch.recut(0, 10 ** 9, 32)
+    assert sch.info()["n_parts"] == 1 and sch.info()["lanes_per_row"] == 32
+    y = sch.execute(Lv, Mv, b=b, x_save=xs)
+    sch.check()
+    assert col_rel_err(host(y), y_ref) < 1e-12
+    res = autotune.tune(sch, lambda: sch.execute(Lv, Mv, b=b, x_save=xs), which=0, budget_s=2.0, use_cache=False)
+    assert res["ms"] > 0 and res["lanes"] in autotune.DEFAULT_LANES
+    resa = autotune.tune(sch, lambda: sch.adjoint(Lv, Mv, gy, saved=xs), which=1, budget_s=2.0, use_cache=False)
+    inf = sch.info()
+    assert inf["lanes_per_row"] == res["lanes"] and inf["adj_lanes_per_row"] == resa["lanes"]
+    y = sch.execute(Lv, Mv, b=b, x_save=xs)
+    gb = sch.adjoint(Lv, Mv, gy, saved=xs)
+    sch.check()
+    sch.validate()
+    assert col_rel_err(host(y), y_ref) < 1e-12
+    assert col_rel_err(host(gb), gb_ref) < 1e-12
+    # the re-cut schedule equals the oracle's cut for the same target and wide threshold
+    got = sch.export(0)
+    ref = oracle.schedule(oracle.SEP, oracle.COST_SEP, w.L, w.M, inf["part_cost_target"], wide=inf["wide_cost"])
+    assert np.array_equal(got["part_ptr"], ref["part_ptr"])
+    assert p0 > 0

@@ -47,9 +47,10 @@ def test_schedule_matches_oracle(wname, pair, target):
     info = sch.info()
     for which, (kind, what) in enumerate([KIND_OF[pair]] + ([ADJ_OF[pair]] if want_adj else [])):
         C = info["part_cost_target"] if which == 0 else info["adj_part_cost_target"]
+        W = info["wide_cost"] if which == 0 else info["adj_wide_cost"]
         if target:
             assert C == target
-        ref = oracle.schedule(kind, what, L, M, C)
+        ref = oracle.schedule(kind, what, L, M, C, wide=W)
         got = sch.export(which)
         assert np.array_equal(got["level"], ref["level"]), f"levels differ ({wname}, {pair}, dir {which})"
         assert got["depth"] == ref["depth"]

@@ -137,10 +137,25 @@ def test_costs_hand_computed():
     assert oracle.costs(oracle.COST_IC0_TRSV, L).tolist() == [3, 6, 10]
     assert oracle.costs(oracle.COST_SPMV_TRSV, L, M).tolist() == [4, 4, 5]
     # column counts: L^T rows 3,2,1; M^T rows 1,1,2
-    assert oracle.costs(oracle.COST_PAIRED_T, L, M).tolist() == [1 + 3 + 1 + 2 + 1, 1 + 2 + 2 + 1 + 1,
-                                                                 2 + 1 + 3 + 1 + 1]
-    assert oracle.costs(oracle.COST_SEP_T, L, M).tolist() == [3 + 1 + 2 + 1, 2 + 2 + 1 + 1, 1 + 3 + 1 + 1,
-                                                              2, 2, 3]
+    assert oracle.costs(oracle.COST_PAIRED_T, L, M).tolist() == [1 + 3 + 1, 1 + 2 + 1, 2 + 1 + 1]
+    assert oracle.costs(oracle.COST_SEP_T, L, M).tolist() == [3 + 1, 2 + 1, 1 + 1, 2, 2, 3]
+
+
+def test_partition_isolates_wide_items():
+    # items costing more than the wide threshold form partitions of their own
+    w = I.spmv_trsv_powerlaw(n=3000, k=1, mean=8, lmax=200, halfband=400, seed=6)
+    s = oracle.schedule(oracle.PAIRED, oracle.COST_SPMV_TRSV, w.L, w.M, 60, wide=40)
+    o, pp, c = s["order"], s["part_ptr"], s["cost"]
+    v = (o.view(np.uint32) & 0x7FFFFFFF).astype(np.int64)
+    wide = c[v] > 40
+    assert wide.any() and not wide.all()
+    for p in range(len(pp) - 1):
+        seg = wide[pp[p]:pp[p + 1]]
+        if seg.any():
+            assert len(seg) == 1
+    plain = oracle.schedule(oracle.PAIRED, oracle.COST_SPMV_TRSV, w.L, w.M, 60)
+    assert len(plain["part_ptr"]) < len(pp)
+    assert oracle.validate(oracle.PAIRED, w.L, None, o, pp) == 0
 
 
 def test_validator_catches_planted_mistakes():

@@ -324,7 +324,7 @@ def run_gpu(args):
         kt *= 2
     launch_opts = dict(lanes_per_row=args.lanes, blocks_per_sm=args.blocks_per_sm, epoch_flags=args.epoch_flags,
                        part_cost_target=args.part_cost, dynamic_queue=args.dynamic_queue,
-                       rhs_tile=kt if wl["k"] > 1 else 0)
+                       rhs_tile=kt if wl["k"] > 1 else 0, team_lanes=args.team)
     g = Gpu(wl, args.dtype, device, launch_opts)
     fns = [g.fwd] + ([g.adj] if wl["adj"] else [])
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device) if wl["fits_l2"] else None
@@ -563,6 +563,7 @@ def main():
     ap.add_argument("--part-cost", type=int, default=0, help="partition cost target (0 = auto)")
     ap.add_argument("--epoch-flags", action="store_true", help="publish through epoch flags even for k = 1")
     ap.add_argument("--dynamic-queue", action="store_true", help="draw partitions from a ticket counter")
+    ap.add_argument("--team", type=int, default=0, help="lanes per partition team: 8 or 32 (0 = auto)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the default launch shape)")
     ap.add_argument("--tune-seconds", type=float, default=8.0, help="time budget of each autotuning search")
     args = ap.parse_args()

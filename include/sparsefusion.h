@@ -87,7 +87,8 @@ typedef struct {
     int32_t blocks_per_sm;    /* resident executor blocks per SM; 0 = occupancy limit  */
     uint64_t timeout_ns;      /* limit of one dependence wait on the GPU; 0 = 2 s    */
     uint32_t flags;           /* SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE  */
-    uint32_t reserved2;       /* must be 0 */
+    int32_t team_lanes;       /* lanes of the unit that runs one partition: 8 or 32
+                                 (several teams per warp); 0 = 32 */
 } sf_options;
 
 /* Opaque fused schedule (§3.1 "fused partitioning", the FusedSchedule of Figure 3b).
@@ -197,6 +198,7 @@ typedef struct {
                                           partition of their own (0: none) */
     int64_t cost_total, adj_cost_total; /* sum of the vertex costs c(v) of each schedule */
     int32_t adj_lanes_per_row, reserved2;
+    int32_t team_lanes, adj_team_lanes;
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -216,11 +218,11 @@ sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_
                                  int32_t blocks_per_sm, int32_t epoch_flags);
 
 /* Re-cuts the partitions (§3.1 coarsening) of the forward (which = 0), adjoint (1) or both
- * (-1) schedules for a new cost target (0 = automatic) and, when lanes_per_row != 0, a new
- * lane count; levels and order are kept. Synchronises `stream` before and after; no launch
+ * (-1) schedules for a new cost target (0 = automatic) and, when non-zero, a new lane count
+ * per row and per team (8 or 32); levels and order are kept. Synchronises `stream` before and after; no launch
  * of this schedule may be pending on another stream. Used by autotuning. */
 sf_status sf_schedule_recut(sf_schedule *sch, int32_t which, int64_t part_cost_target,
-                            int32_t lanes_per_row, void *stream);
+                            int32_t lanes_per_row, int32_t team_lanes, void *stream);
 
 /* Sets the time limit of one dependence wait (0 = 2 s). */
 sf_status sf_schedule_set_timeout(sf_schedule *sch, uint64_t timeout_ns);

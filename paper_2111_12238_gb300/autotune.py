@@ -20,6 +20,7 @@ from . import sparsefusion as sf
 
 DEFAULT_LANES = (1, 2, 4, 8, 16, 32)
 DEFAULT_ITEMS = (2, 4, 8, 16, 32)
+DEFAULT_TEAMS = (8, 32)
 
 
 def _cache_path() -> str:
@@ -73,12 +74,13 @@ def _time(run: Callable[[], object], reps: int) -> float:
 
 
 def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype: torch.dtype = torch.float64,
-         k: int = 1, lanes: Sequence[int] = DEFAULT_LANES, items: Sequence[int] = DEFAULT_ITEMS, reps: int = 3,
+         k: int = 1, lanes: Sequence[int] = DEFAULT_LANES, items: Sequence[int] = DEFAULT_ITEMS,
+         teams: Sequence[int] = DEFAULT_TEAMS, reps: int = 3,
          budget_s: float = 20.0, use_cache: bool = True) -> Dict:
-    """Chooses lanes per row and items per partition for `which` (0 forward, 1 adjoint) of
+    """Chooses lanes per row, team width and items per partition for `which` (0 forward, 1 adjoint) of
     `sched`, timing `run()` (one execution) for every candidate within `budget_s` seconds.
     Leaves the schedule cut and launched with the best candidate and returns
-    dict(lanes, items, part_cost_target, ms, trials, cached)."""
+    dict(lanes, items, team, part_cost_target, ms, trials, cached)."""
     inf = sched.info()
     nv = inf["n_items"] if which == 0 else inf["adj_n_items"]
     cost_total = inf["cost_total"] if which == 0 else inf["adj_cost_total"]
@@ -91,25 +93,26 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     cache = _load_cache(path) if use_cache else {}
     if use_cache and key in cache:
         best = cache[key]
-        sched.recut(which, best["part_cost_target"], best["lanes"])
+        sched.recut(which, best["part_cost_target"], best["lanes"], best.get("team", 0))
         return dict(best, cached=True)
-    cands = [(L, p) for L in lanes if L >= kt for p in items if p <= max(1, 32 // L) * 4]
+    cands = [(L, p, T) for L in lanes if L >= kt for T in teams if T >= L for p in items
+             if p <= max(1, T // L) * 4]
     # start from the default shape, then the rest
-    cands.sort(key=lambda c: (abs(c[0] - max(1, kt)), abs(c[1] - 8)))
+    cands.sort(key=lambda c: (abs(c[0] - max(1, kt)), c[2] != 32, abs(c[1] - 8)))
     t0 = time.perf_counter()
     trials = []
     best = None
-    for L, p in cands:
+    for L, p, T in cands:
         if trials and time.perf_counter() - t0 > budget_s:
             break
         C = max(1, p * mean)
-        sched.recut(which, C, L)
+        sched.recut(which, C, L, T)
         ms = _time(run, reps)
         sched.check()
-        trials.append({"lanes": L, "items": p, "part_cost_target": C, "ms": ms})
+        trials.append({"lanes": L, "items": p, "team": T, "part_cost_target": C, "ms": ms})
         if best is None or ms < best["ms"]:
             best = trials[-1]
-    sched.recut(which, best["part_cost_target"], best["lanes"])
+    sched.recut(which, best["part_cost_target"], best["lanes"], best["team"])
     if use_cache:
         cache = _load_cache(path)
         cache[key] = best

@@ -64,6 +64,7 @@ struct Dir {
     unsigned char *part_wide = nullptr;
     long long W = 0;            // items of cost > W run on a whole warp (0: none)
     int lpr = 1;                // lanes per row of this direction's launches
+    int team = 8;               // lanes of a team (the unit that runs a partition)
     int *cost = nullptr;        // c(v) of every vertex (kept for re-cutting)
     long long cost_total = 0;
     unsigned *flags = nullptr;
@@ -106,6 +107,7 @@ struct sf_schedule {
     Dir fwd, adj;
     int lpr = 4, kt = 0;
     int blocks_per_sm = 0;
+    int team = 0;               // 0: automatic (whole-warp teams)
     bool epoch_flags = false;
     bool dynamic_queue = false;
     unsigned long long timeout_ns = 2000000000ull;
@@ -127,8 +129,9 @@ sf_status validate_options(const sf_options *o) {
         return fail(SF_ERR_INVALID_ARG, "lanes_per_row must be 0 or a power of two in [1, 32]");
     if (o->rhs_tile != 0 && !is_pow2_upto32(o->rhs_tile))
         return fail(SF_ERR_INVALID_ARG, "rhs_tile must be 0 or a power of two in [1, 32]");
-    if (o->g2_placement != 0 || o->reserved2 != 0)
-        return fail(SF_ERR_INVALID_ARG, "g2_placement and reserved fields must be 0");
+    if (o->g2_placement != 0) return fail(SF_ERR_INVALID_ARG, "g2_placement must be 0");
+    if (o->team_lanes != 0 && o->team_lanes != 8 && o->team_lanes != 32)
+        return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     if (o->blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
     if (o->flags & ~(SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE))
         return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
@@ -163,8 +166,8 @@ sf_status copy_pattern(sf_schedule *S, const sf_csr *src, DevCsr &dst, cudaStrea
 }
 
 // Cost prefix and partition cut of one direction (the part of the inspection that the
-// launch shape influences): C_user > 0 is the cost target, else about max(1, G/4) items
-// per partition with G = 32 / lanes the groups of a warp.
+// launch shape influences): C_user > 0 is the cost target, else about one round of a
+// team's groups (at most eight items).
 sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Arena &tmp) {
     const long long nv = d.nv;
     long long *cs = (long long *)tmp.alloc(sizeof(long long) * nv);
@@ -175,9 +178,9 @@ sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Aren
     if (e != cudaSuccess) return from_cuda(e, "cost prefix");
     d.cost_total = total;
     long long C = C_user;
-    if (C <= 0) {
+    if (C <= 0) {   // about one round of a team's groups, at most eight items
         const long long mean = std::max<long long>(1, (total + nv - 1) / nv);
-        C = (long long)std::max(1, (32 / d.lpr) / 4) * mean;
+        C = (long long)std::max(1, std::min(d.team / d.lpr, 8)) * mean;
     }
     d.C = C;
     // rows much longer than a group's lanes can cover quickly get the whole warp
@@ -191,6 +194,7 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     const int n = S->n;
     d.kind = kind;
     d.lpr = S->lpr;
+    d.team = S->team ? std::max(S->team, d.lpr) : 32;
     d.nv = (kind == K_SEP || kind == K_SEP_T) ? 2LL * n : (long long)n;
     const long long nv = d.nv;
     d.level = (int *)S->keep.alloc(sizeof(int) * nv);
@@ -269,6 +273,7 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
     }
     S->kt = o.rhs_tile;
     if (S->kt > S->lpr) S->lpr = S->kt;
+    S->team = o.team_lanes;
     int kind = K_PAIRED, what = 5;
     switch (S->pair) {
         case SF_TRSV_SPMV: kind = K_SEP; what = 0; break;
@@ -344,17 +349,17 @@ sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void 
     return SF_OK;
 }
 
-int occupancy(int mode, int dtype, int lpr, bool vf) {
+int occupancy(int mode, int dtype, int lpr, bool vf, int team) {
     static std::mutex mu;
-    static int cache[M_COUNT][2][6][2] = {};
+    static int cache[M_COUNT][2][6][2][2] = {};
     int li = 0;
     while ((1 << li) < lpr) ++li;
     std::lock_guard<std::mutex> lk(mu);
-    int &c = cache[mode][dtype][li][vf ? 1 : 0];
+    int &c = cache[mode][dtype][li][vf ? 1 : 0][team == 8 ? 0 : 1];
     if (!c) {
-        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf);
-        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) c = occupancy_adj(mode, dtype, lpr, vf);
-        else c = occupancy_pair(mode, dtype, lpr, vf);
+        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf, team);
+        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) c = occupancy_adj(mode, dtype, lpr, vf, team);
+        else c = occupancy_pair(mode, dtype, lpr, vf, team);
     }
     return c;
 }
@@ -374,6 +379,7 @@ void *value_flag_buffer(int mode, const ExecArgs &a) {
 sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int k, ExecArgs &a, cudaStream_t s) {
     const int kt = S->kt ? std::min(S->kt, 32) : std::min(pow2_ceil(k), 32);
     const int lpr = std::max(d.lpr, kt);
+    const int team = lpr <= 8 ? d.team : 32;
     a.order = d.order;
     a.part_ptr = d.part_ptr;
     a.part_wide = d.part_wide;
@@ -401,16 +407,17 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     void *vbuf = value_flag_buffer(mode, a);
     const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
     if (vf) SF_CK(cudaMemsetAsync(vbuf, 0xff, (size_t)S->n * (dt == SF_F64 ? 8 : 4), s), "value-flag reset");
-    int per_sm = occupancy(mode, dtype, lpr, vf);
+    int per_sm = occupancy(mode, dtype, lpr, vf, team);
     if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
     long long blocks = (long long)per_sm * S->sms;
-    blocks = std::min<long long>(blocks, ((long long)d.n_parts + 7) / 8);
+    const long long teams_per_block = 8LL * (32 / team);
+    blocks = std::min<long long>(blocks, ((long long)d.n_parts + teams_per_block - 1) / teams_per_block);
     blocks = std::max<long long>(blocks, 1);
     cudaError_t e;
-    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, (int)blocks, s, a);
+    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, team, (int)blocks, s, a);
     else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
-        e = launch_exec_adj(mode, dtype, lpr, vf, (int)blocks, s, a);
-    else e = launch_exec_pair(mode, dtype, lpr, vf, (int)blocks, s, a);
+        e = launch_exec_adj(mode, dtype, lpr, vf, team, (int)blocks, s, a);
+    else e = launch_exec_pair(mode, dtype, lpr, vf, team, (int)blocks, s, a);
     if (e != cudaSuccess) return from_cuda(e, "executor launch");
     return SF_OK;
 }
@@ -735,6 +742,8 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     }
     info->lanes_per_row = S->fwd.lpr;
     info->adj_lanes_per_row = S->adj.lpr;
+    info->team_lanes = S->fwd.team;
+    info->adj_team_lanes = S->adj.team;
     info->rhs_tile = S->kt;
     info->part_cost_target = S->fwd.C;
     info->packing = S->packing;
@@ -775,6 +784,8 @@ SF_API sf_status sf_schedule_set_launch(sf_schedule *S, int32_t lanes_per_row, i
     S->lpr = lpr;
     S->fwd.lpr = lpr;
     S->adj.lpr = lpr;
+    if (S->fwd.team < lpr) S->fwd.team = 32;
+    if (S->adj.team < lpr) S->adj.team = 32;
     S->kt = kt;
     if (blocks_per_sm) S->blocks_per_sm = blocks_per_sm;
     if (epoch_flags >= 0) S->epoch_flags = epoch_flags == 1;
@@ -782,12 +793,14 @@ SF_API sf_status sf_schedule_set_launch(sf_schedule *S, int32_t lanes_per_row, i
 }
 
 SF_API sf_status sf_schedule_recut(sf_schedule *S, int32_t which, int64_t part_cost_target, int32_t lanes_per_row,
-                                   void *stream) {
+                                   int32_t team_lanes, void *stream) {
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
     if (part_cost_target < 0) return fail(SF_ERR_INVALID_ARG, "part_cost_target must be >= 0");
     if (lanes_per_row && !is_pow2_upto32(lanes_per_row)) return fail(SF_ERR_INVALID_ARG, "bad lanes_per_row");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    if (team_lanes != 0 && team_lanes != 8 && team_lanes != 32)
+        return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     cudaStream_t s = (cudaStream_t)stream;
     SF_CK(cudaStreamSynchronize(s), "recut");      // no launch of this schedule may be in flight
     Arena tmp;
@@ -795,6 +808,8 @@ SF_API sf_status sf_schedule_recut(sf_schedule *S, int32_t which, int64_t part_c
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;
         if (lanes_per_row) dirs[w]->lpr = std::max(lanes_per_row, S->kt);
+        if (team_lanes) dirs[w]->team = std::max(team_lanes, dirs[w]->lpr);
+        else if (dirs[w]->team < dirs[w]->lpr) dirs[w]->team = 32;
         sf_status st = cut_dir(S, *dirs[w], part_cost_target, s, tmp);
         if (st != SF_OK) return st;
     }

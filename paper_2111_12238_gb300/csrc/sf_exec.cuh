@@ -485,45 +485,55 @@ __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, un
 }
 
 constexpr int kExecThreads = 256;
+#ifndef SF_MIN_BLOCKS
+#define SF_MIN_BLOCKS 1
+#endif
 
-// Next ticket of a warp (lane 0 draws it; the caller broadcasts it when needed, so the
-// atomic's latency overlaps the current partition's work).
-__device__ __forceinline__ int draw_ticket(const ExecArgs &a, int lane) {
-    if (lane != 0) return 0;
+// Next ticket of a team (its first lane draws it; the caller broadcasts it when needed, so
+// the atomic's latency overlaps the current partition's work).
+__device__ __forceinline__ int draw_ticket(const ExecArgs &a, int tl) {
+    if (tl != 0) return 0;
     return ld_relaxed_u32(&a.st->abort) ? a.n_parts : (int)atomicAdd(&a.st->ticket, 1u);
 }
 
-template <int MODE, typename T, int LPR, bool VF>
-__global__ void __launch_bounds__(kExecThreads) k_exec(const ExecArgs a) {
-    constexpr int G = 32 / LPR;
+// A warp is split into 32/TEAM teams of TEAM lanes; a team runs one partition at a time
+// with TEAM/LPR groups of LPR lanes (one item per group per round). Teams are the units of
+// the partition assignment, so small partitions do not leave lanes of a warp idle.
+template <int MODE, typename T, int LPR, bool VF, int TEAM>
+__global__ void __launch_bounds__(kExecThreads, SF_MIN_BLOCKS) k_exec(const ExecArgs a) {
+    static_assert(LPR <= TEAM && TEAM <= 32, "groups fit in a team");
+    constexpr int G = TEAM / LPR;
+    constexpr int NT = 32 / TEAM;
     const int lane = threadIdx.x & 31;
-    const int grp = lane / LPR, gl = lane % LPR, gbase = grp * LPR;
+    const int tl = lane % TEAM, tbase = lane - tl;
+    const unsigned tmask = (TEAM == 32) ? 0xffffffffu : (((1u << TEAM) - 1u) << tbase);
+    const int grp = tl / LPR, gl = tl % LPR, gbase = tbase + grp * LPR;
     const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << gbase);
     const unsigned epoch = ld_relaxed_u32(&a.st->epoch);
+    const int nteams = gridDim.x * (blockDim.x >> 5) * NT;
+    const int team = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NT + lane / TEAM;
     bool ok = true;
-    // A warp holds its current partition and the ticket of its next one. Both are drawn
-    // in ticket order, so the smallest unfinished partition held by any warp is always a
-    // current one whose dependences are all finished: progress is preserved.
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int p = a.dynamic ? __shfl_sync(0xffffffffu, draw_ticket(a, lane), 0) : wid;
+    // A team holds its current partition (and with tickets the ticket of its next one);
+    // every team runs its partitions in increasing order, so the smallest unfinished
+    // partition is always being run by a team whose dependences are all finished.
+    int p = a.dynamic ? __shfl_sync(tmask, draw_ticket(a, tl), tbase) : team;
     while (p < a.n_parts) {
-        const int pn_lane0 = a.dynamic ? draw_ticket(a, lane) : 0;
+        const int pn_first = a.dynamic ? draw_ticket(a, tl) : 0;
         const int q0 = __ldg(a.part_ptr + p), q1 = __ldg(a.part_ptr + p + 1);
-        if (LPR < 32 && a.part_wide[p]) {
-            // a long row: the whole warp runs it (the cut gives it a partition of its own)
+        if (LPR < TEAM && a.part_wide[p]) {
+            // a long row: the whole team runs it (the cut gives it a partition of its own)
             const unsigned o = (unsigned)__ldg(a.order + q0);
-            if (ok) ok = run_item<MODE, T, 32, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, lane, 0,
-                                                   0xffffffffu);
+            if (ok) ok = run_item<MODE, T, TEAM, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl, tbase,
+                                                     tmask);
         } else {
             for (int q = q0 + grp; q < q1 && ok; q += G) {
                 const unsigned o = (unsigned)__ldg(a.order + q);
                 ok = run_item<MODE, T, LPR, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
             }
         }
-        if (!__all_sync(0xffffffffu, ok)) break;
-        if (a.dynamic) p = __shfl_sync(0xffffffffu, pn_lane0, 0);
-        else p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : p + nwarps;
+        if (!__all_sync(tmask, ok)) break;
+        if (a.dynamic) p = __shfl_sync(tmask, pn_first, tbase);
+        else p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : p + nteams;
     }
     __syncwarp();
     if (lane == 0) {
@@ -537,42 +547,53 @@ __global__ void __launch_bounds__(kExecThreads) k_exec(const ExecArgs a) {
     }
 }
 
-template <int MODE, bool VF>
-const void *kernel_for(int dtype, int lpr) {
+template <int MODE, bool VF, int TEAM>
+const void *kernel_for_team(int dtype, int lpr) {
     if (dtype == 0) {
         switch (lpr) {
-            case 1: return (const void *)k_exec<MODE, double, 1, VF>;
-            case 2: return (const void *)k_exec<MODE, double, 2, VF>;
-            case 4: return (const void *)k_exec<MODE, double, 4, VF>;
-            case 8: return (const void *)k_exec<MODE, double, 8, VF>;
-            case 16: return (const void *)k_exec<MODE, double, 16, VF>;
-            case 32: return (const void *)k_exec<MODE, double, 32, VF>;
+            case 1: return (const void *)k_exec<MODE, double, 1, VF, TEAM>;
+            case 2: return (const void *)k_exec<MODE, double, 2, VF, TEAM>;
+            case 4: return (const void *)k_exec<MODE, double, 4, VF, TEAM>;
+            case 8: return (const void *)k_exec<MODE, double, 8, VF, TEAM>;
+        }
+        if constexpr (TEAM == 32) {
+            if (lpr == 16) return (const void *)k_exec<MODE, double, 16, VF, 32>;
+            if (lpr == 32) return (const void *)k_exec<MODE, double, 32, VF, 32>;
         }
     } else {
         switch (lpr) {
-            case 1: return (const void *)k_exec<MODE, float, 1, VF>;
-            case 2: return (const void *)k_exec<MODE, float, 2, VF>;
-            case 4: return (const void *)k_exec<MODE, float, 4, VF>;
-            case 8: return (const void *)k_exec<MODE, float, 8, VF>;
-            case 16: return (const void *)k_exec<MODE, float, 16, VF>;
-            case 32: return (const void *)k_exec<MODE, float, 32, VF>;
+            case 1: return (const void *)k_exec<MODE, float, 1, VF, TEAM>;
+            case 2: return (const void *)k_exec<MODE, float, 2, VF, TEAM>;
+            case 4: return (const void *)k_exec<MODE, float, 4, VF, TEAM>;
+            case 8: return (const void *)k_exec<MODE, float, 8, VF, TEAM>;
+        }
+        if constexpr (TEAM == 32) {
+            if (lpr == 16) return (const void *)k_exec<MODE, float, 16, VF, 32>;
+            if (lpr == 32) return (const void *)k_exec<MODE, float, 32, VF, 32>;
         }
     }
     return nullptr;
 }
 
-template <int MODE>
-const void *kernel_for_mode(int dtype, int lpr, bool vf) {
-    if constexpr (mode_has_vf(MODE)) {
-        if (vf) return kernel_for<MODE, true>(dtype, lpr);
-    }
-    return kernel_for<MODE, false>(dtype, lpr);
+// Teams of 8 lanes serve lanes-per-row up to 8; wider rows use whole-warp teams.
+template <int MODE, bool VF>
+const void *kernel_for(int dtype, int lpr, int team) {
+    if (team == 8 && lpr <= 8) return kernel_for_team<MODE, VF, 8>(dtype, lpr);
+    return kernel_for_team<MODE, VF, 32>(dtype, lpr);
 }
 
-// Launches k_exec<MODE, T, LPR, VF> for a runtime (dtype, lanes-per-row, value flags).
 template <int MODE>
-cudaError_t launch_mode(int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a) {
-    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf);
+const void *kernel_for_mode(int dtype, int lpr, bool vf, int team) {
+    if constexpr (mode_has_vf(MODE)) {
+        if (vf) return kernel_for<MODE, true>(dtype, lpr, team);
+    }
+    return kernel_for<MODE, false>(dtype, lpr, team);
+}
+
+// Launches k_exec for a runtime (dtype, lanes-per-row, value flags, team lanes).
+template <int MODE>
+cudaError_t launch_mode(int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s, const ExecArgs &a) {
+    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf, team);
     if (!f) return cudaErrorInvalidValue;
     void *args[] = {(void *)&a};
     if (a.dynamic) return cudaLaunchKernel(f, dim3(blocks), dim3(kExecThreads), args, 0, s);
@@ -580,9 +601,9 @@ cudaError_t launch_mode(int dtype, int lpr, bool vf, int blocks, cudaStream_t s,
 }
 
 template <int MODE>
-int blocks_per_sm_mode(int dtype, int lpr, bool vf) {
+int blocks_per_sm_mode(int dtype, int lpr, bool vf, int team) {
     int nb = 0;
-    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf);
+    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf, team);
     if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kExecThreads, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }

@@ -67,12 +67,15 @@ struct ExecArgs {
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
 // Static assignment needs every block resident: those launches are cooperative.
-cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a);
-cudaError_t launch_exec_pair(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a);
-cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int blocks, cudaStream_t s, const ExecArgs &a);
-int occupancy_fwd(int mode, int dtype, int lpr, bool vf);
-int occupancy_pair(int mode, int dtype, int lpr, bool vf);
-int occupancy_adj(int mode, int dtype, int lpr, bool vf);
+cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
+                            const ExecArgs &a);
+cudaError_t launch_exec_pair(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
+                            const ExecArgs &a);
+cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
+                            const ExecArgs &a);
+int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team);
+int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team);
+int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team);
 // Adjoint helpers: dst[t] = src[perm[t]] (values in transposed order), and the value
 // gradients out[e] = sign * sum_c coef[i*k+c] * vec[col(e)*k+c] over the rows i of a pattern.
 cudaError_t launch_gather_vals(int dtype, long long nnz, const int *perm, const void *src, void *dst, cudaStream_t s);

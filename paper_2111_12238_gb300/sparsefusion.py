@@ -35,7 +35,7 @@ class SfCsr(C.Structure):
 class SfOptions(C.Structure):
     _fields_ = [("part_cost_target", C.c_int64), ("lanes_per_row", C.c_int32), ("rhs_tile", C.c_int32),
                 ("g2_placement", C.c_int32), ("blocks_per_sm", C.c_int32), ("timeout_ns", C.c_uint64),
-                ("flags", C.c_uint32), ("reserved2", C.c_uint32)]
+                ("flags", C.c_uint32), ("team_lanes", C.c_int32)]
 
 
 class SfInfo(C.Structure):
@@ -49,7 +49,8 @@ class SfInfo(C.Structure):
                 ("reuse_ratio", C.c_double), ("inspect_ms", C.c_double),
                 ("wide_cost", C.c_int64), ("adj_wide_cost", C.c_int64),
                 ("cost_total", C.c_int64), ("adj_cost_total", C.c_int64),
-                ("adj_lanes_per_row", C.c_int32), ("reserved2", C.c_int32)]
+                ("adj_lanes_per_row", C.c_int32), ("reserved2", C.c_int32),
+                ("team_lanes", C.c_int32), ("adj_team_lanes", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -77,7 +78,7 @@ _SIGS = {
     "sf_schedule_export": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "sf_schedule_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "sf_schedule_set_timeout": (C.c_int, [_P, C.c_uint64]),
-    "sf_schedule_recut": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_int32, _P]),
+    "sf_schedule_recut": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, _P]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
@@ -176,13 +177,14 @@ class DeviceCsr:
 
 
 def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm=0,
-             epoch_flags=False, dynamic_queue=False) -> SfOptions:
+             epoch_flags=False, dynamic_queue=False, team_lanes=0) -> SfOptions:
     o = SfOptions()
     o.part_cost_target = int(part_cost_target)
     o.lanes_per_row = int(lanes_per_row)
     o.rhs_tile = int(rhs_tile)
     o.timeout_ns = int(timeout_ns)
     o.blocks_per_sm = int(blocks_per_sm)
+    o.team_lanes = int(team_lanes)
     o.flags = ((SF_WANT_ADJOINT if want_adjoint else 0) | (SF_EPOCH_FLAGS if epoch_flags else 0)
                | (SF_DYNAMIC_QUEUE if dynamic_queue else 0))
     return o
@@ -252,10 +254,10 @@ class Schedule:
                                                      int(blocks_per_sm), int(epoch_flags)),
                "sf_schedule_set_launch")
 
-    def recut(self, which=-1, part_cost_target=0, lanes_per_row=0, stream=None):
-        """Re-cuts the partitions for a new cost target and lane count (levels and order kept)."""
+    def recut(self, which=-1, part_cost_target=0, lanes_per_row=0, team_lanes=0, stream=None):
+        """Re-cuts the partitions for a new cost target and lane counts (levels and order kept)."""
         _check(load_library().sf_schedule_recut(self.handle, int(which), int(part_cost_target), int(lanes_per_row),
-                                                _stream(stream)), "sf_schedule_recut")
+                                                int(team_lanes), _stream(stream)), "sf_schedule_recut")
 
     def set_timeout(self, ns: int):
         _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")
@@ -294,10 +296,10 @@ class Schedule:
 
 def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjoint=False, part_cost_target=0,
             lanes_per_row=0, rhs_tile=0, timeout_ns=0, blocks_per_sm=0, epoch_flags=False,
-            dynamic_queue=False, stream=None) -> Schedule:
+            dynamic_queue=False, team_lanes=0, stream=None) -> Schedule:
     lib = load_library()
     o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
-                 dynamic_queue)
+                 dynamic_queue, team_lanes)
     Ls = L.struct()
     Ms = M.struct() if M is not None else None
     h = C.c_void_p()
@@ -309,10 +311,11 @@ def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjo
 
 def inspect_batched(pair: str, Ls: Sequence[DeviceCsr], Ms: Optional[Sequence[DeviceCsr]] = None, *,
                     want_adjoint=False, part_cost_target=0, lanes_per_row=0, rhs_tile=0, timeout_ns=0,
-                    blocks_per_sm=0, epoch_flags=False, dynamic_queue=False, stream=None) -> Schedule:
+                    blocks_per_sm=0, epoch_flags=False, dynamic_queue=False, team_lanes=0,
+                    stream=None) -> Schedule:
     lib = load_library()
     o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
-                 dynamic_queue)
+                 dynamic_queue, team_lanes)
     cnt = len(Ls)
     la = (SfCsr * cnt)(*[x.struct() for x in Ls])
     ma = (SfCsr * cnt)(*[x.struct() for x in Ms]) if Ms is not None else None

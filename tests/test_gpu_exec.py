@@ -253,3 +253,24 @@ def test_recut_and_autotune_keep_results_exact():
     ref = oracle.schedule(oracle.SEP, oracle.COST_SEP, w.L, w.M, inf["part_cost_target"], wide=inf["wide_cost"])
     assert np.array_equal(got["part_ptr"], ref["part_ptr"])
     assert p0 > 0
+
+
+@pytest.mark.parametrize("team,lpr", [(8, 1), (8, 4), (8, 8), (32, 1), (32, 8)])
+def test_team_widths(team, lpr):
+    need_cuda()
+    w = _lap3d(12, 1)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    gb_ref, gL_ref, gM_ref = oracle.adj_trsv_spmv(w.L, w.M, x_ref, w.gy)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, lanes_per_row=lpr,
+                     team_lanes=team)
+    inf = sch.info()
+    assert inf["team_lanes"] == team and inf["adj_team_lanes"] == team
+    Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
+    xs = torch.empty_like(b)
+    y = sch.execute(Lv, Mv, b=b, x_save=xs)
+    gL, gM = torch.empty_like(Lv), torch.empty_like(Mv)
+    gb = sch.adjoint(Lv, Mv, t(w.gy), saved=xs, gL=gL, gM=gM)
+    sch.check()
+    assert col_rel_err(host(y), y_ref) < 1e-12
+    assert col_rel_err(host(gb), gb_ref) < 1e-12
+    assert vec_rel_err(host(gL), gL_ref) < 1e-12 and vec_rel_err(host(gM), gM_ref) < 1e-12

@@ -324,7 +324,8 @@ def run_gpu(args):
         kt *= 2
     launch_opts = dict(lanes_per_row=args.lanes, blocks_per_sm=args.blocks_per_sm, epoch_flags=args.epoch_flags,
                        part_cost_target=args.part_cost, dynamic_queue=args.dynamic_queue,
-                       rhs_tile=kt if wl["k"] > 1 else 0, team_lanes=args.team)
+                       rhs_tile=kt if wl["k"] > 1 else 0, team_lanes=args.team, block_rows=args.block_rows,
+                       exec_mode=args.exec_mode)
     g = Gpu(wl, args.dtype, device, launch_opts)
     fns = [g.fwd] + ([g.adj] if wl["adj"] else [])
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device) if wl["fits_l2"] else None
@@ -470,6 +471,8 @@ def run_gpu(args):
         "inspect_ms": g.inspect_s * 1e3,
         "ner_vs_unfused": (g.inspect_s * 1e3 / (un_ms - fwd_ms)) if un_ms > fwd_ms else None,
         "lanes_per_row": info["lanes_per_row"], "n_parts": info["n_parts"],
+        "exec": {"fwd": info["exec_mode"], "adj": info["adj_exec_mode"], "block_rows": info["block_rows"],
+                 "n_blocks": info["n_blocks"], "block_lanes": info["block_lanes"]},
         "tuned": tuned,
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -564,6 +567,8 @@ def main():
     ap.add_argument("--epoch-flags", action="store_true", help="publish through epoch flags even for k = 1")
     ap.add_argument("--dynamic-queue", action="store_true", help="draw partitions from a ticket counter")
     ap.add_argument("--team", type=int, default=0, help="lanes per partition team: 8 or 32 (0 = auto)")
+    ap.add_argument("--block-rows", type=int, default=0, help="rows per block of the row-block executor")
+    ap.add_argument("--exec-mode", type=int, default=0, help="0 auto, 1 partitions, 2 row blocks")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the default launch shape)")
     ap.add_argument("--tune-seconds", type=float, default=8.0, help="time budget of each autotuning search")
     args = ap.parse_args()

@@ -89,6 +89,10 @@ typedef struct {
     uint32_t flags;           /* SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE  */
     int32_t team_lanes;       /* lanes of the unit that runs one partition: 8 or 32
                                  (several teams per warp); 0 = 32 */
+    int32_t block_rows;       /* rows per block of the row-block executor; 0 = min(8192, n) */
+    int32_t exec_mode;        /* 0 (automatic) and 1: partitions; 2: row blocks (k = 1 with
+                                 value flags; the call fails when a block does not fit in
+                                 shared memory). The autotuner chooses between them. */
 } sf_options;
 
 /* Opaque fused schedule (§3.1 "fused partitioning", the FusedSchedule of Figure 3b).
@@ -199,6 +203,10 @@ typedef struct {
     int64_t cost_total, adj_cost_total; /* sum of the vertex costs c(v) of each schedule */
     int32_t adj_lanes_per_row, reserved2;
     int32_t team_lanes, adj_team_lanes;
+    int32_t block_rows, n_blocks, adj_block_rows, adj_n_blocks;
+    int32_t exec_mode, adj_exec_mode, block_lanes, adj_block_lanes;
+    int32_t block_segments, adj_block_segments;   /* level segments of the row-block order */
+    int32_t block_threads, adj_block_threads;     /* threads per row-block CTA */
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -224,11 +232,33 @@ sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_
 sf_status sf_schedule_recut(sf_schedule *sch, int32_t which, int64_t part_cost_target,
                             int32_t lanes_per_row, int32_t team_lanes, void *stream);
 
+/* Row-block executor (k = 1 with value flags, exec_mode 2): blocks of B consecutive rows
+ * (in decreasing row order for the adjoint), each run by one CTA that keeps the block's
+ * values in shared memory, so dependences inside a block never leave the SM; the CTA runs
+ * one level segment at a time between barriers. A pre-pass computes each row's
+ * independent part and 1 / L_ii, so first-kernel rows finish as (c - sum) * (1 / L_ii)
+ * (one rounding more than a division). Rebuilds the block
+ * order of the forward (0), adjoint (1) or both (-1) schedules for block_rows rows
+ * (0 keeps the current size), sets exec_mode (-1 keeps; 0 automatic, 1 partitions,
+ * 2 row blocks) and the row-block lanes per row (1, 2, 4 or 32; 0 keeps). Synchronises
+ * `stream` before and after. */
+sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,
+                              int32_t lanes_per_row, void *stream);
+
+/* Copies a row-block schedule to HOST buffers: order[n_items] (row | kernel << 31, sorted
+ * by (block, level, kernel, row)), block_ptr[n_blocks+1], seg_ptr[block_segments+1] (first
+ * position of every level segment: a maximal run of positions with the same block and
+ * level, run by one CTA between two barriers) and block_seg[n_blocks+1] (first segment of
+ * every block). Any pointer may be NULL. Synchronous. */
+sf_status sf_schedule_export_blocks(const sf_schedule *sch, int32_t which, int32_t *order,
+                                    int32_t *block_ptr, int32_t *seg_ptr, int32_t *block_seg);
+
 /* Sets the time limit of one dependence wait (0 = 2 s). */
 sf_status sf_schedule_set_timeout(sf_schedule *sch, uint64_t timeout_ns);
 
 /* Testing hook: swaps two entries of the forward order (positions q1 and q2) on the
- * device, producing a schedule that may violate a dependence. An execution of such a
+ * device, in the partition order and in the row-block order, producing a schedule that may
+ * violate a dependence. An execution of such a
  * schedule ends through the bounded dependence wait with SF_ERR_TIMEOUT reported by
  * sf_schedule_check, never by a hang. */
 sf_status sf_schedule_debug_swap(sf_schedule *sch, int64_t q1, int64_t q2);

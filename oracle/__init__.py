@@ -64,6 +64,8 @@ def _load():
                          "orc_order", "orc_validate"):
                 getattr(lib, name).restype = C.c_int
             lib.orc_partition.restype = C.c_int64
+            lib.orc_block_order.restype = C.c_int64
+            lib.orc_block_segments.restype = C.c_int64
             lib.orc_reuse_ratio.restype = C.c_double
             lib.orc_reuse_ratio.argtypes = [C.c_int32, C.c_int64, C.c_int64, C.c_int64]
             _lib = lib
@@ -302,6 +304,40 @@ def partition(order_, n, cost, target, wide=0):
     P = lib.orc_partition(C.c_int64(len(o)), C.c_int32(n), po, c.ctypes.data_as(C.c_void_p),
                           C.c_int64(int(target)), C.c_int64(int(wide)), ppp)
     return pp[: P + 1].copy()
+
+
+def block_order(kind, L, M, level, B):
+    """(order, block_ptr) of the row-block schedule with blocks of B rows."""
+    lib = _load()
+    n = L.n_rows
+    kl, lrp, lci, _ = _csr(L)
+    if M is not None:
+        km, mrp, mci, _ = _csr(M)
+    else:
+        mrp = mci = None
+    lev, pl = _i32(level)
+    o, po = _out(len(lev), np.int32)
+    nb = -(-n // int(B))
+    bp, pbp = _out(nb + 1, np.int32)
+    got = lib.orc_block_order(C.c_int32(kind), C.c_int32(n), lrp, lci, mrp, mci, pl, C.c_int64(int(B)), po, pbp)
+    if got < 0:
+        raise OracleError(got, "block_order")
+    return o, bp
+
+
+def block_segments(kind, n, order_, block_ptr, level):
+    """(seg_ptr, block_seg) of a row-block order: runs of positions with one block and level."""
+    lib = _load()
+    o, po = _i32(order_)
+    bp, pbp = _i32(block_ptr)
+    lev, pl = _i32(level)
+    nb = len(bp) - 1
+    sp, psp = _out(len(o) + 1, np.int32)
+    bs, pbs = _out(nb + 1, np.int32)
+    ns = lib.orc_block_segments(C.c_int32(kind), C.c_int32(n), C.c_int64(nb), po, pbp, pl, psp, pbs)
+    if ns < 0:
+        raise OracleError(ns, "block_segments")
+    return sp[:ns + 1].copy(), bs
 
 
 def validate(kind, L, M, order_, part_ptr):

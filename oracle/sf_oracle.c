@@ -372,6 +372,77 @@ int64_t orc_partition(int64_t nv, int32_t n, const int32_t *order, const int64_t
     return P;
 }
 
+/* Row-block order (the schedule of the row-block executor). Rows are cut into blocks of B
+ * consecutive rows, taken in increasing row order for the forward kinds and in decreasing
+ * row order for the transposed ones (so that every dependence points to the same or an
+ * earlier block). A vertex belongs to the block of its own row for the first kernel; a
+ * second-kernel vertex belongs to the latest block among the rows it reads (block 0 if it
+ * reads none). Vertices are ordered by (block, level, tag, row). Writes order[nv] and
+ * block_ptr[nb+1]; returns nb = ceil(n / B). */
+int64_t orc_block_order(int32_t kind, int32_t n, const int32_t *lrp, const int32_t *lci,
+                        const int32_t *mrp, const int32_t *mci, const int32_t *level, int64_t B,
+                        int32_t *order, int32_t *block_ptr) {
+    const int64_t nb = (n + B - 1) / B;
+    const int64_t nv = (kind == 0 || kind == 3) ? 2LL * n : n;
+    const int rev = kind == 2 || kind == 3;
+    int64_t *blk = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
+    if (!blk) return -1;
+    for (int32_t i = 0; i < n; ++i) blk[i] = rev ? nb - 1 - i / B : i / B;
+    if (kind == 0)                       /* SpMV row i reads x_j for M_ij != 0 */
+        for (int32_t i = 0; i < n; ++i) {
+            int64_t b = 0;
+            for (int64_t e = mrp[i]; e < mrp[i + 1]; ++e)
+                if (blk[mci[e]] > b) b = blk[mci[e]];
+            blk[n + i] = b;
+        }
+    if (kind == 3) {                     /* A^T row j reads lam_i for A_ij != 0 */
+        for (int32_t j = 0; j < n; ++j) blk[n + j] = 0;
+        for (int32_t i = 0; i < n; ++i)
+            for (int64_t e = mrp[i]; e < mrp[i + 1]; ++e)
+                if (blk[i] > blk[n + mci[e]]) blk[n + mci[e]] = blk[i];
+    }
+    int32_t depth = 0;
+    for (int64_t v = 0; v < nv; ++v)
+        if (level[v] + 1 > depth) depth = level[v] + 1;
+    const int64_t nkeys = nb * depth;
+    int64_t *start = (int64_t *)calloc((size_t)nkeys + 1, sizeof(int64_t));
+    if (!start) { free(blk); return -1; }
+    for (int64_t v = 0; v < nv; ++v) start[blk[v] * depth + level[v] + 1]++;
+    for (int64_t t = 0; t < nkeys; ++t) start[t + 1] += start[t];
+    for (int64_t b = 0; b <= nb; ++b) block_ptr[b] = (int32_t)start[b * depth];
+    for (int64_t v = 0; v < nv; ++v) {
+        uint32_t tag = (uint32_t)(v / n), row = (uint32_t)(v % n);
+        order[start[blk[v] * depth + level[v]]++] = (int32_t)(row | (tag << 31));
+    }
+    free(start);
+    free(blk);
+    return nb;
+}
+
+/* Level segments of a row-block order: a new segment starts at the first position of every
+ * block and wherever the level changes from the previous position. The vertices of one
+ * segment share a block and a level, so none depends on another (§2.2: every edge of the
+ * joint DAG goes from a lower wavefront to a higher one). Writes seg_ptr[nseg+1] (capacity
+ * nv+1) and block_seg[nb+1]; returns nseg. */
+int64_t orc_block_segments(int32_t kind, int32_t n, int64_t nb, const int32_t *order, const int32_t *block_ptr,
+                           const int32_t *level, int32_t *seg_ptr, int32_t *block_seg) {
+    const int64_t nv = (kind == 0 || kind == 3) ? 2LL * n : n;
+    int64_t ns = 0;
+    int32_t prev = -1;
+    for (int64_t b = 0; b < nb; ++b) {
+        block_seg[b] = (int32_t)ns;
+        for (int64_t q = block_ptr[b]; q < block_ptr[b + 1]; ++q) {
+            const uint32_t o = (uint32_t)order[q];
+            const int64_t v = (int64_t)(o >> 31) * n + (o & 0x7fffffffu);
+            if (q == block_ptr[b] || level[v] != prev) seg_ptr[ns++] = (int32_t)q;
+            prev = level[v];
+        }
+    }
+    block_seg[nb] = (int32_t)ns;
+    seg_ptr[ns] = (int32_t)nv;
+    return ns;
+}
+
 /* Validity of a schedule (§3.2: a fused schedule must honour every intra- and
  * inter-kernel dependence): order is a permutation of the vertices, every DAG and F edge
  * u -> v has pos(u) < pos(v), partitions are contiguous, non-empty and cover the order.

@@ -1,9 +1,11 @@
 """Autotuner of the executor's launch shape.
 
-For one schedule and one way of running it, times candidate (lanes per row, items per
-partition) pairs on the GPU and keeps the fastest. A candidate is applied without
-re-inspecting: ``sf_schedule_recut`` re-cuts the partitions for the new cost target
-(items per partition x mean vertex cost) and lane count, keeping levels and order.
+For one schedule and one way of running it, times candidate launch shapes on the GPU and
+keeps the fastest: for one right-hand side the row-block executor with several block sizes
+and lane counts, and the partition executor with several (lanes per row, team width, items
+per partition). Candidates are applied without re-inspecting: ``sf_schedule_reblock``
+rebuilds the row-block order, ``sf_schedule_recut`` re-cuts the partitions for a new cost
+target (items per partition x mean vertex cost); levels are kept.
 Results are cached in a JSON file (``SF_TUNE_CACHE``, default
 ``~/.cache/sparsefusion/tune.json``) keyed by the schedule's shape and the GPU's name.
 """
@@ -21,6 +23,8 @@ from . import sparsefusion as sf
 DEFAULT_LANES = (1, 2, 4, 8, 16, 32)
 DEFAULT_ITEMS = (2, 4, 8, 16, 32)
 DEFAULT_TEAMS = (8, 32)
+DEFAULT_BLOCK_ROWS = (1024, 2048, 4096, 8192, 16384)
+DEFAULT_BLOCK_LANES = (1, 2, 4, 32)
 
 
 def _cache_path() -> str:
@@ -73,14 +77,25 @@ def _time(run: Callable[[], object], reps: int) -> float:
     return times[len(times) // 2]
 
 
+def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
+    """Applies one candidate launch shape to direction `which` of the schedule."""
+    if c["exec"] == "blocks":
+        sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
+    else:
+        c["part_cost_target"] = max(1, c["items"] * mean)
+        sched.recut(which, c["part_cost_target"], c["lanes"], c["team"])
+        sched.reblock(which, 0, 1, 0)
+
+
 def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype: torch.dtype = torch.float64,
          k: int = 1, lanes: Sequence[int] = DEFAULT_LANES, items: Sequence[int] = DEFAULT_ITEMS,
-         teams: Sequence[int] = DEFAULT_TEAMS, reps: int = 3,
-         budget_s: float = 20.0, use_cache: bool = True) -> Dict:
-    """Chooses lanes per row, team width and items per partition for `which` (0 forward, 1 adjoint) of
+         teams: Sequence[int] = DEFAULT_TEAMS, blocks: bool = True,
+         block_rows: Sequence[int] = DEFAULT_BLOCK_ROWS, block_lanes: Sequence[int] = DEFAULT_BLOCK_LANES,
+         reps: int = 3, budget_s: float = 20.0, use_cache: bool = True) -> Dict:
+    """Chooses the executor and its launch shape for `which` (0 forward, 1 adjoint) of
     `sched`, timing `run()` (one execution) for every candidate within `budget_s` seconds.
-    Leaves the schedule cut and launched with the best candidate and returns
-    dict(lanes, items, team, part_cost_target, ms, trials, cached)."""
+    Leaves the schedule set to the best candidate and returns it as a dict (exec, its
+    parameters, ms) with the list of trials and whether it came from the cache."""
     inf = sched.info()
     nv = inf["n_items"] if which == 0 else inf["adj_n_items"]
     cost_total = inf["cost_total"] if which == 0 else inf["adj_cost_total"]
@@ -93,26 +108,37 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     cache = _load_cache(path) if use_cache else {}
     if use_cache and key in cache:
         best = cache[key]
-        sched.recut(which, best["part_cost_target"], best["lanes"], best.get("team", 0))
+        _apply(sched, which, best, mean)
         return dict(best, cached=True)
-    cands = [(L, p, T) for L in lanes if L >= kt for T in teams if T >= L for p in items
-             if p <= max(1, T // L) * 4]
-    # start from the default shape, then the rest
-    cands.sort(key=lambda c: (abs(c[0] - max(1, kt)), c[2] != 32, abs(c[1] - 8)))
+    cands = []
+    if k == 1 and blocks:
+        n = inf["n"]
+        for B in block_rows:
+            if B <= 2 * max(n, 1):
+                for L in block_lanes:
+                    cands.append({"exec": "blocks", "block_rows": B, "block_lanes": L})
+    pc = [(L, p, T) for L in lanes if L >= kt for T in teams if T >= L for p in items if p <= max(1, T // L) * 4]
+    pc.sort(key=lambda c: (abs(c[0] - max(1, kt)), c[2] != 32, abs(c[1] - 8)))
+    cands += [{"exec": "partitions", "lanes": L, "items": p, "team": T} for L, p, T in pc]
     t0 = time.perf_counter()
     trials = []
     best = None
-    for L, p, T in cands:
+    for c in cands:
         if trials and time.perf_counter() - t0 > budget_s:
             break
-        C = max(1, p * mean)
-        sched.recut(which, C, L, T)
-        ms = _time(run, reps)
+        try:
+            _apply(sched, which, c, mean)
+            ms = _time(run, reps)
+        except sf.SparseFusionError:
+            # a row-block size whose shared-memory footprint does not fit this direction
+            if c["exec"] != "blocks":
+                raise
+            continue
         sched.check()
-        trials.append({"lanes": L, "items": p, "team": T, "part_cost_target": C, "ms": ms})
+        trials.append(dict(c, ms=ms))
         if best is None or ms < best["ms"]:
             best = trials[-1]
-    sched.recut(which, best["part_cost_target"], best["lanes"], best["team"])
+    _apply(sched, which, best, mean)
     if use_cache:
         cache = _load_cache(path)
         cache[key] = best

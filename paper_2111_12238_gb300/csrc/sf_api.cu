@@ -67,6 +67,17 @@ struct Dir {
     int team = 8;               // lanes of a team (the unit that runs a partition)
     int *cost = nullptr;        // c(v) of every vertex (kept for re-cutting)
     long long cost_total = 0;
+    // row-block schedule (k = 1 executor with shared-memory dependences)
+    int B = 0, nb = 0;
+    int blpr = 1;               // lanes per row of the row-block executor (1, 4 or 32)
+    int exec_mode = 0;          // 0 automatic (partitions), 1 partitions, 2 row blocks
+    int *border = nullptr;      // order by (block, level, kernel, row)
+    int2 *bdesc = nullptr;      // per position: entry range of the row waited on
+    int *block_ptr = nullptr;
+    int *seg_ptr = nullptr;     // level segments of the row-block order (n_segs + 1)
+    int *block_seg = nullptr;   // first segment of every block (nb + 1)
+    int n_segs = 0, max_seg = 0;
+    void *aux = nullptr;        // (c_i, 1 / L_ii) per row, written by the row-block pre-pass
     unsigned *flags = nullptr;
     ExecState *st = nullptr;
 };
@@ -108,6 +119,8 @@ struct sf_schedule {
     int lpr = 4, kt = 0;
     int blocks_per_sm = 0;
     int team = 0;               // 0: automatic (whole-warp teams)
+    int block_rows = 0;         // rows per block of the row-block executor (0: automatic)
+    int exec_mode = 0;          // 0 automatic, 1 partitions, 2 row blocks
     bool epoch_flags = false;
     bool dynamic_queue = false;
     unsigned long long timeout_ns = 2000000000ull;
@@ -132,6 +145,9 @@ sf_status validate_options(const sf_options *o) {
     if (o->g2_placement != 0) return fail(SF_ERR_INVALID_ARG, "g2_placement must be 0");
     if (o->team_lanes != 0 && o->team_lanes != 8 && o->team_lanes != 32)
         return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
+    if (o->block_rows < 0 || o->block_rows > (1 << 20))
+        return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
+    if (o->exec_mode < 0 || o->exec_mode > 2) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0, 1 or 2");
     if (o->blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
     if (o->flags & ~(SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE))
         return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
@@ -190,6 +206,42 @@ sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Aren
     return SF_OK;
 }
 
+// Row-block order of one direction for blocks of B rows (0: automatic, 8192 rows or n).
+sf_status block_dir(sf_schedule *S, Dir &d, int B, cudaStream_t s, Arena &tmp) {
+    if (B <= 0) B = (int)std::min<long long>(8192, ((long long)S->n + 31) / 32 * 32);
+    const int nb_new = (int)(((long long)S->n + B - 1) / B);
+    if (!d.block_ptr || nb_new > d.nb) {
+        d.block_ptr = (int *)S->keep.alloc(sizeof(int) * ((size_t)nb_new + 1));
+        d.block_seg = (int *)S->keep.alloc(sizeof(int) * ((size_t)nb_new + 1));
+        if (!d.block_ptr || !d.block_seg) return fail(SF_ERR_OOM, "inspector: out of device memory");
+    }
+    if (!d.seg_ptr) {
+        d.seg_ptr = (int *)S->keep.alloc(sizeof(int) * ((size_t)d.nv + 1));
+        d.aux = S->keep.alloc(sizeof(double) * 2 * (size_t)S->n);
+        if (!d.seg_ptr || !d.aux) return fail(SF_ERR_OOM, "inspector: out of device memory");
+    }
+    const bool sep = d.kind == K_SEP || d.kind == K_SEP_T;
+    cudaError_t e = build_block_order(d.kind, S->n, d.nv, B, d.depth, d.level, sep ? &S->M : nullptr,
+                                      (d.kind == K_SEP_T) ? &S->MT : nullptr, d.border, d.block_ptr, d.seg_ptr,
+                                      d.block_seg, &d.nb, &d.n_segs, &d.max_seg, s, tmp);
+    if (e != cudaSuccess) return from_cuda(e, "row-block order");
+    if (!d.bdesc) {
+        d.bdesc = (int2 *)S->keep.alloc(sizeof(int2) * d.nv);
+        if (!d.bdesc) return fail(SF_ERR_OOM, "inspector: out of device memory");
+    }
+    e = build_block_desc(d.kind, d.nv, d.border, S->L, sep ? &S->M : nullptr, S->LT,
+                         (d.kind == K_SEP_T) ? &S->MT : nullptr, d.bdesc, s);
+    if (e != cudaSuccess) return from_cuda(e, "row-block descriptors");
+    d.B = B;
+    return SF_OK;
+}
+
+// Threads of a row-block CTA: enough groups for the widest level segment, 64 to 512.
+int block_threads(const Dir &d) {
+    const long long want = ((long long)std::max(d.max_seg, 1) * d.blpr + 31) / 32 * 32;
+    return (int)std::min<long long>(kBlockMaxThreads, std::max<long long>(64, want));
+}
+
 sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user, cudaStream_t s, Arena &tmp) {
     const int n = S->n;
     d.kind = kind;
@@ -239,6 +291,12 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     if (e != cudaSuccess) return from_cuda(e, "vertex costs");
     sf_status st = cut_dir(S, d, C_user, s, tmp);
     if (st != SF_OK) return st;
+    d.border = (int *)S->keep.alloc(sizeof(int) * nv);
+    if (!d.border) return fail(SF_ERR_OOM, "inspector: out of device memory");
+    st = block_dir(S, d, S->block_rows, s, tmp);
+    if (st != SF_OK) return st;
+    d.exec_mode = S->exec_mode;
+    d.blpr = d.lpr <= 1 ? 1 : (d.lpr <= 2 ? 2 : (d.lpr <= 16 ? 4 : 32));
     d.present = true;
     return SF_OK;
 }
@@ -274,6 +332,8 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
     S->kt = o.rhs_tile;
     if (S->kt > S->lpr) S->lpr = S->kt;
     S->team = o.team_lanes;
+    S->block_rows = o.block_rows;
+    S->exec_mode = o.exec_mode;
     int kind = K_PAIRED, what = 5;
     switch (S->pair) {
         case SF_TRSV_SPMV: kind = K_SEP; what = 0; break;
@@ -406,6 +466,31 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     const int dtype = dt == SF_F64 ? 0 : 1;
     void *vbuf = value_flag_buffer(mode, a);
     const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
+    // the row-block executor serves one right-hand side with value flags (its pre-pass
+    // resets the published vector)
+    if (vf && d.exec_mode == 2 && d.nb > 0) {
+        const int threads = block_threads(d);
+        const int occ = block_exec_occupancy(mode, dtype, d.blpr, std::min(d.B, S->n), threads);
+        if (occ > 0) {
+            a.aux = d.aux;
+            a.order = d.border;
+            a.bdesc = d.bdesc;
+            a.block_ptr = d.block_ptr;
+            a.seg_ptr = d.seg_ptr;
+            a.block_seg = d.block_seg;
+            a.block_rows = d.B;
+            a.n_blocks = d.nb;
+            a.block_rev = (d.kind == K_PAIRED_T || d.kind == K_SEP_T) ? 1 : 0;
+            int per_sm = occ;
+            if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
+            long long blocks = std::min<long long>((long long)per_sm * S->sms, d.nb);
+            blocks = std::max<long long>(blocks, 1);
+            cudaError_t e = launch_block_exec(mode, dtype, d.blpr, (int)blocks, threads, s, a);
+            if (e != cudaSuccess) return from_cuda(e, "row-block executor launch");
+            return SF_OK;
+        }
+        return fail(SF_ERR_UNSUPPORTED, "row blocks of %d rows do not fit in shared memory", d.B);
+    }
     if (vf) SF_CK(cudaMemsetAsync(vbuf, 0xff, (size_t)S->n * (dt == SF_F64 ? 8 : 4), s), "value-flag reset");
     int per_sm = occupancy(mode, dtype, lpr, vf, team);
     if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
@@ -744,6 +829,18 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     info->adj_lanes_per_row = S->adj.lpr;
     info->team_lanes = S->fwd.team;
     info->adj_team_lanes = S->adj.team;
+    info->block_rows = S->fwd.B;
+    info->n_blocks = S->fwd.nb;
+    info->adj_block_rows = S->adj.B;
+    info->adj_n_blocks = S->adj.nb;
+    info->exec_mode = S->fwd.exec_mode;
+    info->adj_exec_mode = S->adj.exec_mode;
+    info->block_lanes = S->fwd.blpr;
+    info->adj_block_lanes = S->adj.blpr;
+    info->block_segments = S->fwd.n_segs;
+    info->adj_block_segments = S->adj.n_segs;
+    info->block_threads = S->fwd.present ? block_threads(S->fwd) : 0;
+    info->adj_block_threads = S->adj.present ? block_threads(S->adj) : 0;
     info->rhs_tile = S->kt;
     info->part_cost_target = S->fwd.C;
     info->packing = S->packing;
@@ -817,6 +914,46 @@ SF_API sf_status sf_schedule_recut(sf_schedule *S, int32_t which, int64_t part_c
     return SF_OK;
 }
 
+SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t block_rows, int32_t exec_mode,
+                                     int32_t lanes_per_row, void *stream) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (block_rows < 0 || block_rows > (1 << 20)) return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
+    if (exec_mode < -1 || exec_mode > 2) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1, 0, 1 or 2");
+    if (lanes_per_row != 0 && lanes_per_row != 1 && lanes_per_row != 2 && lanes_per_row != 4 && lanes_per_row != 32)
+        return fail(SF_ERR_INVALID_ARG, "row-block lanes per row must be 1, 2, 4 or 32");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    cudaStream_t s = (cudaStream_t)stream;
+    SF_CK(cudaStreamSynchronize(s), "reblock");
+    Arena tmp;
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w) {
+        if ((which != -1 && which != w) || !dirs[w]->present) continue;
+        if (block_rows && block_rows != dirs[w]->B) {
+            sf_status st = block_dir(S, *dirs[w], block_rows, s, tmp);
+            if (st != SF_OK) return st;
+        }
+        if (exec_mode >= 0) dirs[w]->exec_mode = exec_mode;
+        if (lanes_per_row) dirs[w]->blpr = lanes_per_row;
+    }
+    SF_CK(cudaStreamSynchronize(s), "reblock");
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_export_blocks(const sf_schedule *S, int32_t which, int32_t *order, int32_t *block_ptr,
+                                           int32_t *seg_ptr, int32_t *block_seg) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which != 0 && which != 1) return fail(SF_ERR_INVALID_ARG, "which must be 0 or 1");
+    const Dir &d = which ? S->adj : S->fwd;
+    if (!d.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    if (order) SF_CK(cudaMemcpy(order, d.border, sizeof(int) * d.nv, cudaMemcpyDeviceToHost), "export");
+    if (block_ptr) SF_CK(cudaMemcpy(block_ptr, d.block_ptr, sizeof(int) * (d.nb + 1), cudaMemcpyDeviceToHost), "export");
+    if (seg_ptr)
+        SF_CK(cudaMemcpy(seg_ptr, d.seg_ptr, sizeof(int) * ((size_t)d.n_segs + 1), cudaMemcpyDeviceToHost), "export");
+    if (block_seg) SF_CK(cudaMemcpy(block_seg, d.block_seg, sizeof(int) * (d.nb + 1), cudaMemcpyDeviceToHost), "export");
+    return SF_OK;
+}
+
 SF_API sf_status sf_schedule_set_timeout(sf_schedule *S, uint64_t timeout_ns) {
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     S->timeout_ns = timeout_ns ? timeout_ns : 2000000000ull;
@@ -826,11 +963,22 @@ SF_API sf_status sf_schedule_set_timeout(sf_schedule *S, uint64_t timeout_ns) {
 SF_API sf_status sf_schedule_debug_swap(sf_schedule *S, int64_t q1, int64_t q2) {
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (q1 < 0 || q2 < 0 || q1 >= S->fwd.nv || q2 >= S->fwd.nv) return fail(SF_ERR_INVALID_ARG, "position out of range");
-    int a = 0, b = 0;
-    SF_CK(cudaMemcpy(&a, S->fwd.order + q1, sizeof(int), cudaMemcpyDeviceToHost), "swap");
-    SF_CK(cudaMemcpy(&b, S->fwd.order + q2, sizeof(int), cudaMemcpyDeviceToHost), "swap");
-    SF_CK(cudaMemcpy(S->fwd.order + q1, &b, sizeof(int), cudaMemcpyHostToDevice), "swap");
-    SF_CK(cudaMemcpy(S->fwd.order + q2, &a, sizeof(int), cudaMemcpyHostToDevice), "swap");
+    int *orders[2] = {S->fwd.order, S->fwd.border};
+    for (int *ord : orders) {
+        if (!ord) continue;
+        int a = 0, b = 0;
+        SF_CK(cudaMemcpy(&a, ord + q1, sizeof(int), cudaMemcpyDeviceToHost), "swap");
+        SF_CK(cudaMemcpy(&b, ord + q2, sizeof(int), cudaMemcpyDeviceToHost), "swap");
+        SF_CK(cudaMemcpy(ord + q1, &b, sizeof(int), cudaMemcpyHostToDevice), "swap");
+        SF_CK(cudaMemcpy(ord + q2, &a, sizeof(int), cudaMemcpyHostToDevice), "swap");
+    }
+    if (S->fwd.bdesc) {
+        int2 a, b;
+        SF_CK(cudaMemcpy(&a, S->fwd.bdesc + q1, sizeof(int2), cudaMemcpyDeviceToHost), "swap");
+        SF_CK(cudaMemcpy(&b, S->fwd.bdesc + q2, sizeof(int2), cudaMemcpyDeviceToHost), "swap");
+        SF_CK(cudaMemcpy(S->fwd.bdesc + q1, &b, sizeof(int2), cudaMemcpyHostToDevice), "swap");
+        SF_CK(cudaMemcpy(S->fwd.bdesc + q2, &a, sizeof(int2), cudaMemcpyHostToDevice), "swap");
+    }
     return SF_OK;
 }
 

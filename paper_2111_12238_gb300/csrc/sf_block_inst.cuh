@@ -1,0 +1,38 @@
+// Kernel tables of the row-block executor for one element type (one translation unit per
+// type, so that the two compile in parallel).
+#pragma once
+
+#include "sf_block.cuh"
+
+namespace sf {
+
+template <int MODE, typename T>
+const void *block_kernel_lpr(int lpr) {
+    switch (lpr) {
+        case 1: return (const void *)k_block_exec<MODE, T, 1>;
+        case 2: return (const void *)k_block_exec<MODE, T, 2>;
+        case 4: return (const void *)k_block_exec<MODE, T, 4>;
+        case 32: return (const void *)k_block_exec<MODE, T, 32>;
+        default: return nullptr;
+    }
+}
+
+// lpr == 0 selects the pre-pass of the mode.
+template <typename T>
+const void *block_kernel_t(int mode, int lpr) {
+    switch (mode) {
+        case M_TRSV_SPMV: return lpr ? block_kernel_lpr<M_TRSV_SPMV, T>(lpr) : (const void *)k_block_prep<M_TRSV_SPMV, T>;
+        case M_TRSV: return lpr ? block_kernel_lpr<M_TRSV, T>(lpr) : (const void *)k_block_prep<M_TRSV, T>;
+        case M_SPMV_TRSV: return lpr ? block_kernel_lpr<M_SPMV_TRSV, T>(lpr) : (const void *)k_block_prep<M_SPMV_TRSV, T>;
+        case M_ADJ_TRSV_SPMV:
+            return lpr ? block_kernel_lpr<M_ADJ_TRSV_SPMV, T>(lpr) : (const void *)k_block_prep<M_ADJ_TRSV_SPMV, T>;
+        case M_ADJ_SPMV_TRSV:
+            return lpr ? block_kernel_lpr<M_ADJ_SPMV_TRSV, T>(lpr) : (const void *)k_block_prep<M_ADJ_SPMV_TRSV, T>;
+        default: return nullptr;
+    }
+}
+
+const void *block_kernel_f64(int mode, int lpr);
+const void *block_kernel_f32(int mode, int lpr);
+
+}  // namespace sf

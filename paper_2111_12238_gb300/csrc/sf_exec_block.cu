@@ -1,0 +1,56 @@
+// Row-block executor: double-precision kernels, launch and occupancy (k = 1; one, two, four
+// or thirty-two lanes per row).
+#include <algorithm>
+
+#include "sf_block_inst.cuh"
+
+namespace sf {
+
+const void *block_kernel_f64(int mode, int lpr) { return block_kernel_t<double>(mode, lpr); }
+
+namespace {
+
+const void *block_kernel(int mode, int dtype, int lpr) {
+    return dtype == 0 ? block_kernel_f64(mode, lpr) : block_kernel_f32(mode, lpr);
+}
+
+}  // namespace
+
+size_t block_exec_smem(int mode, int dtype, int block_rows) {
+    (void)mode;
+    return (size_t)block_rows * (dtype == 0 ? 8 : 4);
+}
+
+int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threads) {
+    const void *f = lpr ? block_kernel(mode, dtype, lpr) : nullptr;
+    if (!f || threads < 32 || threads > kBlockMaxThreads || threads % 32) return 0;
+    const size_t smem = block_exec_smem(mode, dtype, block_rows);
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int threads, cudaStream_t s,
+                              const ExecArgs &a) {
+    const void *prep = block_kernel(mode, dtype, 0);
+    const void *f = lpr ? block_kernel(mode, dtype, lpr) : nullptr;
+    if (!prep || !f || threads < 32 || threads > kBlockMaxThreads || threads % 32) return cudaErrorInvalidValue;
+    void *args[] = {(void *)&a};
+    // pre-pass: value-flag reset, independent parts and reciprocal diagonals of all rows
+    const long long pb = std::min<long long>(((long long)a.n + 255) / 256, 65535LL);
+    cudaError_t e = cudaLaunchKernel(prep, dim3((unsigned)std::max<long long>(pb, 1)), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = block_exec_smem(mode, dtype, std::min(a.block_rows, a.n));
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(threads), args, smem, s);
+}
+
+}  // namespace sf

@@ -1,0 +1,6 @@
+// Row-block executor kernels, single precision.
+#include "sf_block_inst.cuh"
+
+namespace sf {
+const void *block_kernel_f32(int mode, int lpr) { return block_kernel_t<float>(mode, lpr); }
+}  // namespace sf

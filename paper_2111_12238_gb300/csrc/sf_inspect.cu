@@ -612,6 +612,140 @@ cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs
     return cudaStreamSynchronize(s);
 }
 
+// ------------------------------------------------------------------------------ row blocks
+// Block of every vertex for the row-block executor: first-kernel rows by their own row
+// (decreasing row order for the transposed kinds), second-kernel rows by the latest block
+// among the rows they read (columns ascend, so that is the last column of an M row, or the
+// first row of an A^T row when blocks run in decreasing row order). key = block*depth+level.
+__global__ void k_block_keys(int kind, int n, long long nv, int B, int nb, int depth, const int *__restrict__ level,
+                             const int *__restrict__ Mrp, const int *__restrict__ Mci,
+                             const int *__restrict__ MTrp, const int *__restrict__ MTci,
+                             unsigned *__restrict__ keys, unsigned *__restrict__ vals, int *__restrict__ bcount) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+        const bool rev = kind == K_PAIRED_T || kind == K_SEP_T;
+        long long b;
+        if (v < n) {
+            b = rev ? nb - 1 - v / B : v / B;
+        } else {
+            const int i = (int)(v - n);
+            if (kind == K_SEP) {
+                const int e0 = Mrp[i], e1 = Mrp[i + 1];
+                b = e1 > e0 ? Mci[e1 - 1] / B : 0;
+            } else {   // K_SEP_T
+                const int e0 = MTrp[i], e1 = MTrp[i + 1];
+                b = e1 > e0 ? nb - 1 - MTci[e0] / B : 0;
+            }
+        }
+        keys[v] = (unsigned)(b * depth + level[v]);
+        vals[v] = (unsigned)v;
+        atomicAdd(&bcount[b], 1);
+    }
+}
+
+// Level segments of the row-block order: maximal runs of positions with the same (block,
+// level) key. A segment's vertices are independent of one another, so the row-block
+// executor runs a segment with all its threads and then crosses one CTA barrier.
+__global__ void k_seg_flags(long long nv, const unsigned *__restrict__ keys, int *__restrict__ flag) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x)
+        flag[q] = (q == 0 || keys[q] != keys[q - 1]) ? 1 : 0;
+}
+
+__global__ void k_seg_ptr(long long nv, const int *__restrict__ flag, const int *__restrict__ segidx,
+                          int *__restrict__ seg_ptr) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
+        if (flag[q]) seg_ptr[segidx[q]] = (int)q;
+        if (q == nv - 1) seg_ptr[segidx[nv]] = (int)nv;
+    }
+}
+
+__global__ void k_seg_width(long long nv, const int *__restrict__ segidx, const int *__restrict__ seg_ptr,
+                            int *__restrict__ maxw) {
+    const int ns = segidx[nv];
+    int w = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += (long long)gridDim.x * blockDim.x)
+        w = max(w, seg_ptr[t + 1] - seg_ptr[t]);
+    for (int off = 16; off >= 1; off >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, off));
+    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(maxw, w);
+}
+
+__global__ void k_block_seg(int nb, long long nv, const int *__restrict__ block_ptr, const int *__restrict__ segidx,
+                            int *__restrict__ block_seg, int *__restrict__ out2) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
+        block_seg[b] = b < nb ? segidx[block_ptr[b]] : segidx[nv];
+        if (b == nb) out2[0] = segidx[nv];
+    }
+}
+
+cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, const int *level, const DevCsr *M,
+                              const DevCsrT *MT, int *order, int *block_ptr, int *seg_ptr, int *block_seg,
+                              int *nb_out, int *n_segs_out, int *max_width_out, cudaStream_t s, Arena &ar) {
+    const int nb = (int)((n + (long long)B - 1) / B);
+    unsigned *keys = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
+    unsigned *vals = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
+    int *cnt = (int *)ar.alloc(sizeof(int) * ((size_t)nb + 1));
+    int *flag = (int *)ar.alloc(sizeof(int) * (size_t)nv);
+    int *segidx = (int *)ar.alloc(sizeof(int) * ((size_t)nv + 1));
+    int *out2 = (int *)ar.alloc(sizeof(int) * 2);
+    if (!keys || !vals || !cnt || !flag || !segidx || !out2) return cudaErrorMemoryAllocation;
+    cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)nb + 1), s);
+    cudaMemsetAsync(out2, 0, sizeof(int) * 2, s);
+    k_block_keys<<<grid_for(nv, 256, 4096), 256, 0, s>>>(kind, n, nv, B, nb, depth, level, M ? M->rowptr : nullptr,
+                                                         M ? M->colidx : nullptr, MT ? MT->t.rowptr : nullptr,
+                                                         MT ? MT->t.colidx : nullptr, keys, vals, cnt);
+    cudaError_t e = radix_sort_pairs(keys, vals, nv, bits_for((unsigned long long)nb * depth - 1), s, ar);
+    if (e != cudaSuccess) return e;
+    k_encode_order<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, n, vals, order);
+    e = scan_excl<int>(cnt, block_ptr, nb, s, ar);
+    if (e != cudaSuccess) return e;
+    k_seg_flags<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, keys, flag);
+    e = scan_excl<int>(flag, segidx, nv, s, ar);
+    if (e != cudaSuccess) return e;
+    k_seg_ptr<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, flag, segidx, seg_ptr);
+    k_seg_width<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, segidx, seg_ptr, out2 + 1);
+    k_block_seg<<<grid_for((long long)nb + 1, 256, 4096), 256, 0, s>>>(nb, nv, block_ptr, segidx, block_seg, out2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int h[2] = {0, 0};
+    e = cudaMemcpyAsync(h, out2, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *nb_out = nb;
+    *n_segs_out = h[0];
+    *max_width_out = h[1];
+    return cudaSuccess;
+}
+
+// Per-position descriptor of the row-block order: the entry range [rs, re) of the row whose
+// entries are waited on (strict lower part of L_i; M_i for a second-kernel row of a forward
+// schedule; strict part of (L^T)_j, i.e. after the diagonal, or (A^T)_j for the transposed
+// ones), so that a round of the row-block executor reads its metadata in one coalesced load.
+__global__ void k_block_desc(int kind, long long nv, const int *__restrict__ order, const int *__restrict__ Lrp,
+                             const int *__restrict__ Mrp, const int *__restrict__ LTrp, const int *__restrict__ MTrp,
+                             int2 *__restrict__ desc) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nv; q += (long long)gridDim.x * blockDim.x) {
+        const unsigned o = (unsigned)order[q];
+        const int row = (int)(o & 0x7fffffffu);
+        const bool tag = (o >> 31) != 0;
+        int2 d;
+        if (kind == K_SEP || kind == K_PAIRED) {
+            if (!tag) d = make_int2(Lrp[row], Lrp[row + 1] - 1);
+            else d = make_int2(Mrp[row], Mrp[row + 1]);
+        } else {
+            if (!tag) d = make_int2(LTrp[row] + 1, LTrp[row + 1]);
+            else d = make_int2(MTrp[row], MTrp[row + 1]);
+        }
+        desc[q] = d;
+    }
+}
+
+cudaError_t build_block_desc(int kind, long long nv, const int *order, const DevCsr &L, const DevCsr *M,
+                             const DevCsrT &LT, const DevCsrT *MT, int2 *desc, cudaStream_t s) {
+    k_block_desc<<<grid_for(nv, 256, 4096), 256, 0, s>>>(kind, nv, order, L.rowptr, M ? M->rowptr : nullptr,
+                                                         LT.t.rowptr, MT ? MT->t.rowptr : nullptr, desc);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------ batching
 __global__ void k_concat(const InstDesc *__restrict__ d, int *__restrict__ rp_out, int *__restrict__ ci_out) {
     const InstDesc in = d[blockIdx.y];

@@ -73,6 +73,11 @@ cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost
                          long long *total, cudaStream_t s, Arena &ar);
 cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs, long long C, long long W,
                            int *part_ptr, unsigned char *part_wide, int *n_parts, cudaStream_t s, Arena &ar);
+cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, const int *level, const DevCsr *M,
+                              const DevCsrT *MT, int *order, int *block_ptr, int *seg_ptr, int *block_seg,
+                              int *nb_out, int *n_segs_out, int *max_width_out, cudaStream_t s, Arena &ar);
+cudaError_t build_block_desc(int kind, long long nv, const int *order, const DevCsr &L, const DevCsr *M,
+                             const DevCsrT &LT, const DevCsrT *MT, int2 *desc, cudaStream_t s);
 cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci_out, long long total_nnz,
                             int total_rows, cudaStream_t s, Arena &ar);
 

@@ -53,6 +53,13 @@ struct ExecArgs {
     int k;
     int kt;                 // right-hand-side columns handled side by side (pow2 <= lanes)
     int dynamic;            // 1: partitions from a ticket counter; 0: static round robin
+    const int *block_ptr;   // row-block executor: first position of each block in `order`
+    const int2 *bdesc;      // row-block executor: entry range of the row each position waits on
+    const int *seg_ptr;     // row-block executor: level segments of `order`
+    const int *block_seg;   // row-block executor: first segment of each block
+    int block_rows;         // rows per block (B)
+    int n_blocks;
+    int block_rev;          // blocks run in decreasing row order (transposed schedules)
     unsigned *flags;
     ExecState *st;
     unsigned long long timeout_ns;
@@ -63,6 +70,7 @@ struct ExecArgs {
     const void *Lv, *Mv, *xin, *b, *gy, *saved;
     const void *LTv, *MTv;              // values of L^T and M^T / A^T in transposed order (adjoint)
     void *y, *xs, *gb, *gx, *gL, *gM;
+    void *aux;                          // row-block executor: (c_i, 1 / L_ii) per row
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
@@ -73,6 +81,13 @@ cudaError_t launch_exec_pair(int mode, int dtype, int lpr, bool vf, int team, in
                             const ExecArgs &a);
 cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
                             const ExecArgs &a);
+// Row-block executor (k = 1): launch and blocks per SM for B rows of shared values and
+// `threads` threads per CTA (a multiple of 32, at most kBlockMaxThreads).
+constexpr int kBlockMaxThreads = 512;
+cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int threads, cudaStream_t s,
+                              const ExecArgs &a);
+int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threads);
+size_t block_exec_smem(int mode, int dtype, int block_rows);
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team);
 int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team);

@@ -35,7 +35,8 @@ class SfCsr(C.Structure):
 class SfOptions(C.Structure):
     _fields_ = [("part_cost_target", C.c_int64), ("lanes_per_row", C.c_int32), ("rhs_tile", C.c_int32),
                 ("g2_placement", C.c_int32), ("blocks_per_sm", C.c_int32), ("timeout_ns", C.c_uint64),
-                ("flags", C.c_uint32), ("team_lanes", C.c_int32)]
+                ("flags", C.c_uint32), ("team_lanes", C.c_int32), ("block_rows", C.c_int32),
+                ("exec_mode", C.c_int32)]
 
 
 class SfInfo(C.Structure):
@@ -50,7 +51,12 @@ class SfInfo(C.Structure):
                 ("wide_cost", C.c_int64), ("adj_wide_cost", C.c_int64),
                 ("cost_total", C.c_int64), ("adj_cost_total", C.c_int64),
                 ("adj_lanes_per_row", C.c_int32), ("reserved2", C.c_int32),
-                ("team_lanes", C.c_int32), ("adj_team_lanes", C.c_int32)]
+                ("team_lanes", C.c_int32), ("adj_team_lanes", C.c_int32),
+                ("block_rows", C.c_int32), ("n_blocks", C.c_int32), ("adj_block_rows", C.c_int32),
+                ("adj_n_blocks", C.c_int32), ("exec_mode", C.c_int32), ("adj_exec_mode", C.c_int32),
+                ("block_lanes", C.c_int32), ("adj_block_lanes", C.c_int32),
+                ("block_segments", C.c_int32), ("adj_block_segments", C.c_int32),
+                ("block_threads", C.c_int32), ("adj_block_threads", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -79,6 +85,8 @@ _SIGS = {
     "sf_schedule_set_launch": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "sf_schedule_set_timeout": (C.c_int, [_P, C.c_uint64]),
     "sf_schedule_recut": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, _P]),
+    "sf_schedule_reblock": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
+    "sf_schedule_export_blocks": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
@@ -177,7 +185,7 @@ class DeviceCsr:
 
 
 def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm=0,
-             epoch_flags=False, dynamic_queue=False, team_lanes=0) -> SfOptions:
+             epoch_flags=False, dynamic_queue=False, team_lanes=0, block_rows=0, exec_mode=0) -> SfOptions:
     o = SfOptions()
     o.part_cost_target = int(part_cost_target)
     o.lanes_per_row = int(lanes_per_row)
@@ -185,6 +193,8 @@ def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns
     o.timeout_ns = int(timeout_ns)
     o.blocks_per_sm = int(blocks_per_sm)
     o.team_lanes = int(team_lanes)
+    o.block_rows = int(block_rows)
+    o.exec_mode = int(exec_mode)
     o.flags = ((SF_WANT_ADJOINT if want_adjoint else 0) | (SF_EPOCH_FLAGS if epoch_flags else 0)
                | (SF_DYNAMIC_QUEUE if dynamic_queue else 0))
     return o
@@ -259,6 +269,27 @@ class Schedule:
         _check(load_library().sf_schedule_recut(self.handle, int(which), int(part_cost_target), int(lanes_per_row),
                                                 int(team_lanes), _stream(stream)), "sf_schedule_recut")
 
+    def reblock(self, which=-1, block_rows=0, exec_mode=-1, lanes_per_row=0, stream=None):
+        """Rebuilds the row-block order for `block_rows` rows per block and/or selects the
+        executor (exec_mode 0 automatic, 1 partitions, 2 row blocks)."""
+        _check(load_library().sf_schedule_reblock(self.handle, int(which), int(block_rows), int(exec_mode),
+                                                  int(lanes_per_row), _stream(stream)), "sf_schedule_reblock")
+
+    def export_blocks(self, which=0) -> dict:
+        inf = self.info()
+        nv = inf["n_items"] if which == 0 else inf["adj_n_items"]
+        nb = inf["n_blocks"] if which == 0 else inf["adj_n_blocks"]
+        ns = inf["block_segments"] if which == 0 else inf["adj_block_segments"]
+        order = np.zeros(nv, dtype=np.int32)
+        bp = np.zeros(nb + 1, dtype=np.int32)
+        sp = np.zeros(ns + 1, dtype=np.int32)
+        bs = np.zeros(nb + 1, dtype=np.int32)
+        _check(load_library().sf_schedule_export_blocks(self.handle, which, order.ctypes.data, bp.ctypes.data,
+                                                        sp.ctypes.data, bs.ctypes.data),
+               "sf_schedule_export_blocks")
+        return dict(order=order, block_ptr=bp, seg_ptr=sp, block_seg=bs,
+                    block_rows=inf["block_rows"] if which == 0 else inf["adj_block_rows"])
+
     def set_timeout(self, ns: int):
         _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")
 
@@ -296,10 +327,10 @@ class Schedule:
 
 def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjoint=False, part_cost_target=0,
             lanes_per_row=0, rhs_tile=0, timeout_ns=0, blocks_per_sm=0, epoch_flags=False,
-            dynamic_queue=False, team_lanes=0, stream=None) -> Schedule:
+            dynamic_queue=False, team_lanes=0, block_rows=0, exec_mode=0, stream=None) -> Schedule:
     lib = load_library()
     o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
-                 dynamic_queue, team_lanes)
+                 dynamic_queue, team_lanes, block_rows, exec_mode)
     Ls = L.struct()
     Ms = M.struct() if M is not None else None
     h = C.c_void_p()
@@ -311,11 +342,11 @@ def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjo
 
 def inspect_batched(pair: str, Ls: Sequence[DeviceCsr], Ms: Optional[Sequence[DeviceCsr]] = None, *,
                     want_adjoint=False, part_cost_target=0, lanes_per_row=0, rhs_tile=0, timeout_ns=0,
-                    blocks_per_sm=0, epoch_flags=False, dynamic_queue=False, team_lanes=0,
-                    stream=None) -> Schedule:
+                    blocks_per_sm=0, epoch_flags=False, dynamic_queue=False, team_lanes=0, block_rows=0,
+                    exec_mode=0, stream=None) -> Schedule:
     lib = load_library()
     o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
-                 dynamic_queue, team_lanes)
+                 dynamic_queue, team_lanes, block_rows, exec_mode)
     cnt = len(Ls)
     la = (SfCsr * cnt)(*[x.struct() for x in Ls])
     ma = (SfCsr * cnt)(*[x.struct() for x in Ms]) if Ms is not None else None

@@ -74,7 +74,8 @@ def test_timeout_is_reported_not_hung(ef):
     D = np.eye(n) * 2 + np.eye(n, k=-1)
     L = dense_to_csr(D)
     b = np.ones((n, 1))
-    sch = sf.inspect("trsv", dev_csr(L), lanes_per_row=32, part_cost_target=10 ** 9, epoch_flags=ef)
+    sch = sf.inspect("trsv", dev_csr(L), lanes_per_row=32, part_cost_target=10 ** 9, epoch_flags=ef,
+                     exec_mode=1)
     assert sch.info()["n_parts"] == 1
     sch.set_timeout(2_000_000)
     sch.debug_swap(0, 1)

@@ -238,10 +238,17 @@ def test_recut_and_autotune_keep_results_exact():
     sch.check()
     assert col_rel_err(host(y), y_ref) < 1e-12
     res = autotune.tune(sch, lambda: sch.execute(Lv, Mv, b=b, x_save=xs), which=0, budget_s=2.0, use_cache=False)
-    assert res["ms"] > 0 and res["lanes"] in autotune.DEFAULT_LANES
     resa = autotune.tune(sch, lambda: sch.adjoint(Lv, Mv, gy, saved=xs), which=1, budget_s=2.0, use_cache=False)
     inf = sch.info()
-    assert inf["lanes_per_row"] == res["lanes"] and inf["adj_lanes_per_row"] == resa["lanes"]
+    # the schedule is left in the winning launch shape of each direction
+    for r, pre in ((res, ""), (resa, "adj_")):
+        assert r["ms"] > 0
+        if r["exec"] == "blocks":
+            assert inf[pre + "exec_mode"] == 2 and inf[pre + "block_lanes"] == r["block_lanes"]
+            assert inf[pre + "block_rows"] == r["block_rows"]
+        else:
+            assert inf[pre + "exec_mode"] == 1 and r["lanes"] in autotune.DEFAULT_LANES
+            assert inf[pre + "lanes_per_row"] == r["lanes"]
     y = sch.execute(Lv, Mv, b=b, x_save=xs)
     gb = sch.adjoint(Lv, Mv, gy, saved=xs)
     sch.check()

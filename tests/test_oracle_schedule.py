@@ -187,3 +187,82 @@ def test_reuse_ratio_table2_golden():
         got = oracle.reuse_ratio(case["pair"], case["n"], case["size_L"], case["size_M"])
         assert got == pytest.approx(float(num) / float(den), rel=1e-15)
         assert (got >= 1.0) == case["interleaved"]
+
+
+@pytest.mark.parametrize("kind", [oracle.SEP, oracle.PAIRED, oracle.PAIRED_T, oracle.SEP_T])
+@pytest.mark.parametrize("B", [1, 7, 64, 10 ** 6])
+def test_block_order_is_a_valid_blocked_linearisation(kind, B):
+    w = I.spmv_trsv_powerlaw(n=500, k=1, mean=6, lmax=30, halfband=60, seed=8)
+    L, M = w.L, w.M
+    useM = M if kind in (oracle.SEP, oracle.SEP_T) else None
+    lev = oracle.levels(kind, L, useM)
+    o, bp = oracle.block_order(kind, L, useM, lev, B)
+    n = L.n_rows
+    nb = -(-n // B)
+    assert len(bp) == nb + 1 and bp[0] == 0 and bp[-1] == len(o)
+    # every DAG and F edge points forward (blocks are contiguous, levels sorted inside)
+    assert oracle.validate(kind, L, useM, o, bp) == 0
+    # first-kernel rows sit in their own row block (reversed for the transposed kinds)
+    rev = kind in (oracle.PAIRED_T, oracle.SEP_T)
+    ov = o.view(np.uint32)
+    for b in range(nb):
+        seg = ov[bp[b]:bp[b + 1]]
+        rows = (seg & 0x7FFFFFFF)[(seg >> 31) == 0].astype(np.int64)
+        want = (nb - 1 - b) if rev else b
+        assert np.all(rows // B == want)
+        v = (seg >> 31).astype(np.int64) * n + (seg & 0x7FFFFFFF)
+        key = lev[v].astype(np.int64) * (2 * n) + v
+        assert np.all(np.diff(key) > 0)           # (level, tag, row) inside a block
+    if B >= n:
+        ref, _ = oracle.order(lev, n)
+        assert np.array_equal(o, ref)             # one block: the plain level order
+
+
+@pytest.mark.parametrize("kind", [oracle.SEP, oracle.PAIRED, oracle.PAIRED_T, oracle.SEP_T])
+@pytest.mark.parametrize("B", [1, 7, 64, 10 ** 6])
+def test_block_segments_are_independent_level_runs(kind, B):
+    w = I.spmv_trsv_powerlaw(n=400, k=1, mean=6, lmax=30, halfband=50, seed=9)
+    L, M = w.L, w.M
+    useM = M if kind in (oracle.SEP, oracle.SEP_T) else None
+    lev = oracle.levels(kind, L, useM)
+    o, bp = oracle.block_order(kind, L, useM, lev, B)
+    n = L.n_rows
+    sp, bs = oracle.block_segments(kind, n, o, bp, lev)
+    ov = o.view(np.uint32)
+    v = (ov >> 31).astype(np.int64) * n + (ov & 0x7FFFFFFF)
+    nb = len(bp) - 1
+    # brute force: the distinct levels of every block, in increasing order, one segment each
+    want_ptr = []
+    want_bs = []
+    for b in range(nb):
+        want_bs.append(len(want_ptr))
+        seen = None
+        for q in range(bp[b], bp[b + 1]):
+            if seen is None or lev[v[q]] != seen:
+                want_ptr.append(q)
+                seen = lev[v[q]]
+    want_bs.append(len(want_ptr))
+    want_ptr.append(len(o))
+    assert sp.tolist() == want_ptr and bs.tolist() == want_bs
+    assert len(sp) - 1 == sum(len(set(lev[v[bp[b]:bp[b + 1]]].tolist())) for b in range(nb))
+    # no vertex of a segment reads another vertex of the same segment: the DAG edges j -> i
+    # (strict lower L, or its transpose) and the F edges never join two positions of a run
+    seg_of = np.zeros(len(o), dtype=np.int64)
+    for s in range(len(sp) - 1):
+        seg_of[sp[s]:sp[s + 1]] = s
+    pos = np.empty(len(o), dtype=np.int64)
+    pos[v] = np.arange(len(o))
+    Lrp, Lci = L.rowptr, L.colidx
+    for i in range(n):
+        for e in range(Lrp[i], Lrp[i + 1] - 1):
+            j = int(Lci[e])
+            a, b_ = (j, i) if kind in (oracle.SEP, oracle.PAIRED) else (i, j)
+            assert seg_of[pos[a]] < seg_of[pos[b_]]
+    if kind == oracle.SEP:
+        for i in range(n):
+            for e in range(M.rowptr[i], M.rowptr[i + 1]):
+                assert seg_of[pos[int(M.colidx[e])]] < seg_of[pos[n + i]]
+    if kind == oracle.SEP_T:
+        for i in range(n):
+            for e in range(M.rowptr[i], M.rowptr[i + 1]):
+                assert seg_of[pos[i]] < seg_of[pos[n + int(M.colidx[e])]]

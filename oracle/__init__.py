@@ -340,27 +340,6 @@ def block_segments(kind, n, order_, block_ptr, level):
     return sp[:ns + 1].copy(), bs
 
 
-def part_keys(kind, L, M, order_, part_ptr):
-    """Key dependence (largest position of an input before the partition, or -1) of every
-    partition of a schedule."""
-    lib = _load()
-    n = L.n_rows
-    kl, lrp, lci, _ = _csr(L)
-    if M is not None:
-        km, mrp, mci, _ = _csr(M)
-    else:
-        mrp = mci = None
-    o, po = _i32(order_)
-    pp, ppp = _i32(part_ptr)
-    P = len(pp) - 1
-    key, pk = _out(P, np.int32)
-    rc = lib.orc_part_keys(C.c_int32(kind), C.c_int32(n), lrp, lci, mrp, mci, po, C.c_int64(len(o)), ppp,
-                           C.c_int64(P), pk)
-    if rc != 0:
-        raise OracleError(rc, "part_keys")
-    return key
-
-
 def validate(kind, L, M, order_, part_ptr):
     lib = _load()
     n = L.n_rows

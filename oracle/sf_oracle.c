@@ -485,50 +485,6 @@ int orc_validate(int32_t kind, int32_t n, const int32_t *lrp, const int32_t *lci
     return rc;
 }
 
-/* Key dependence of every partition: the largest position, among the dependences of the
- * partition's vertices that lie before the partition (edges of the joint DAG, §2.2), or -1
- * when there is none. It is the input of the partition produced last in the level order;
- * the executor waits for it once per partition before the vertices check their own inputs.
- * kind: 0 separated forward, 1 paired forward, 2 paired transposed, 3 separated transposed.
- * Writes key[P]; returns 0, or -1 when out of memory. */
-int orc_part_keys(int32_t kind, int32_t n, const int32_t *lrp, const int32_t *lci, const int32_t *mrp,
-                  const int32_t *mci, const int32_t *order, int64_t nv, const int32_t *part_ptr, int64_t P,
-                  int32_t *key) {
-    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
-    int64_t *part = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
-    if (!pos || !part) { free(pos); free(part); return -1; }
-    for (int64_t q = 0; q < nv; ++q) {
-        const uint32_t o = (uint32_t)order[q];
-        pos[(int64_t)(o >> 31) * n + (o & 0x7fffffffu)] = q;
-    }
-    for (int64_t p = 0; p < P; ++p) {
-        key[p] = -1;
-        for (int64_t q = part_ptr[p]; q < part_ptr[p + 1]; ++q) part[q] = p;
-    }
-    for (int32_t i = 0; i < n; ++i) {
-        for (int64_t e = lrp[i]; e < lrp[i + 1]; ++e) {
-            const int32_t j = lci[e];
-            if (j >= i) continue;
-            /* forward kinds: vertex i reads vertex j; transposed kinds: vertex j reads i */
-            const int64_t u = (kind == 0 || kind == 1) ? j : i;
-            const int64_t v = (kind == 0 || kind == 1) ? i : j;
-            const int64_t pv = part[pos[v]];
-            if (pos[u] < part_ptr[pv] && pos[u] > key[pv]) key[pv] = (int32_t)pos[u];
-        }
-        if (kind == 0 || kind == 3)
-            for (int64_t e = mrp[i]; e < mrp[i + 1]; ++e) {
-                /* SpMV row i reads x_j; A^T row j (gx_j) reads lam_i */
-                const int64_t u = kind == 0 ? mci[e] : i;
-                const int64_t v = kind == 0 ? (int64_t)n + i : (int64_t)n + mci[e];
-                const int64_t pv = part[pos[v]];
-                if (pos[u] < part_ptr[pv] && pos[u] > key[pv]) key[pv] = (int32_t)pos[u];
-            }
-    }
-    free(pos);
-    free(part);
-    return 0;
-}
-
 /* Reuse ratio of Table 2 / §2.2 "Reuse Ratio": common accesses over the larger of the two
  * kernels' accesses, estimated from variable sizes. pair: 0 SpTRSV->SpMV (combination 4),
  * 1 SpIC0->SpTRSV (combination 5), 2 SpMV->SpTRSV (combination 2). size_L, size_M are

@@ -266,46 +266,3 @@ def test_block_segments_are_independent_level_runs(kind, B):
         for i in range(n):
             for e in range(M.rowptr[i], M.rowptr[i + 1]):
                 assert seg_of[pos[i]] < seg_of[pos[n + int(M.colidx[e])]]
-
-
-@pytest.mark.parametrize("kind", [oracle.SEP, oracle.PAIRED, oracle.PAIRED_T, oracle.SEP_T])
-@pytest.mark.parametrize("target", [1, 9, 40])
-def test_part_keys_brute_force(kind, target):
-    # key of a partition = largest position among the inputs of its vertices that lie before
-    # it; inputs enumerated here from dense patterns, independently of the oracle's loops
-    w = I.spmv_trsv_powerlaw(n=160, k=1, mean=5, lmax=12, halfband=25, seed=17)
-    L, M = w.L, w.M
-    n = L.n_rows
-    useM = M if kind in (oracle.SEP, oracle.SEP_T) else None
-    what = {oracle.SEP: oracle.COST_SEP, oracle.PAIRED: oracle.COST_TRSV, oracle.PAIRED_T: oracle.COST_PAIRED_T,
-            oracle.SEP_T: oracle.COST_SEP_T}[kind]
-    sch = oracle.schedule(kind, what, L, M if kind == oracle.PAIRED_T else useM, target)   # PAIRED_T costs read M
-    o, pp = sch["order"], sch["part_ptr"]
-    got = oracle.part_keys(kind, L, useM, o, pp)
-    Ld = np.zeros((n, n), bool)
-    for i in range(n):
-        Ld[i, L.colidx[L.rowptr[i]:L.rowptr[i + 1]]] = True
-    Md = np.zeros((n, n), bool)
-    for i in range(n):
-        Md[i, M.colidx[M.rowptr[i]:M.rowptr[i + 1]]] = True
-    ov = o.view(np.uint32)
-    verts = (ov >> 31).astype(np.int64) * n + (ov & 0x7FFFFFFF)
-    pos = np.empty(len(o), np.int64)
-    pos[verts] = np.arange(len(o))
-
-    def inputs(v):
-        tag, r = divmod(int(v), n)
-        if kind in (oracle.SEP, oracle.PAIRED):
-            cols = np.nonzero(Md[r])[0] if tag else np.nonzero(Ld[r, :r])[0]
-            return cols
-        if tag == 0:                                   # transposed solve row r reads rows i > r
-            return r + 1 + np.nonzero(Ld[r + 1:, r])[0]
-        return np.nonzero(Md[:, r])[0]                 # A^T row r reads lam_i, A_ir != 0
-
-    for p in range(len(pp) - 1):
-        best = -1
-        for q in range(pp[p], pp[p + 1]):
-            for u in inputs(verts[q]):
-                if pos[u] < pp[p]:
-                    best = max(best, int(pos[u]))
-        assert got[p] == best, (p, got[p], best)

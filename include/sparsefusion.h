@@ -207,6 +207,10 @@ typedef struct {
     int32_t exec_mode, adj_exec_mode, block_lanes, adj_block_lanes;
     int32_t block_segments, adj_block_segments;   /* level segments of the row-block order */
     int32_t block_threads, adj_block_threads;     /* threads per row-block CTA */
+    int32_t parts_class0, adj_parts_class0;       /* separated schedules: partitions whose first
+                                                     vertex is a first-kernel row (class 0; 0 for
+                                                     paired schedules) */
+    int32_t split_pct, adj_split_pct;             /* see sf_schedule_set_split */
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -244,6 +248,15 @@ sf_status sf_schedule_recut(sf_schedule *sch, int32_t which, int64_t part_cost_t
  * `stream` before and after. */
 sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,
                               int32_t lanes_per_row, void *stream);
+
+/* Partition classes of the separated schedules (SpTRSV -> SpMV forward, SpMV -> SpTRSV
+ * adjoint): with class0_pct in 1..99 that percent of the executor's teams run the partitions
+ * whose first vertex is a first-kernel row (the solve chain), the other teams run the
+ * partitions that open with a second-kernel row (sinks of the joint DAG), each class round
+ * robin in partition order, so second-kernel rows never occupy a team the chain waits for.
+ * 0 (the default) runs one class. Applies to the forward (0), adjoint (1) or both (-1)
+ * schedules; paired schedules ignore it. No GPU work. */
+sf_status sf_schedule_set_split(sf_schedule *sch, int32_t which, int32_t class0_pct);
 
 /* Copies a row-block schedule to HOST buffers: order[n_items] (row | kernel << 31, sorted
  * by (block, level, kernel, row)), block_ptr[n_blocks+1], seg_ptr[block_segments+1] (first

@@ -3,7 +3,8 @@
 For one schedule and one way of running it, times candidate launch shapes on the GPU and
 keeps the fastest: for one right-hand side the row-block executor with several block sizes
 and lane counts, and the partition executor with several (lanes per row, team width, items
-per partition). Candidates are applied without re-inspecting: ``sf_schedule_reblock``
+per partition), then, for separated schedules, the best partition shape with the teams split
+between the two partition classes (``sf_schedule_set_split``). Candidates are applied without re-inspecting: ``sf_schedule_reblock``
 rebuilds the row-block order, ``sf_schedule_recut`` re-cuts the partitions for a new cost
 target (items per partition x mean vertex cost); levels are kept.
 Results are cached in a JSON file (``SF_TUNE_CACHE``, default
@@ -25,6 +26,7 @@ DEFAULT_ITEMS = (2, 4, 8, 16, 32)
 DEFAULT_TEAMS = (8, 32)
 DEFAULT_BLOCK_ROWS = (1024, 2048, 4096, 8192, 16384)
 DEFAULT_BLOCK_LANES = (1, 2, 4, 32)
+DEFAULT_SPLITS = (50, 65, 80, 90)
 
 
 def _cache_path() -> str:
@@ -81,17 +83,20 @@ def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     """Applies one candidate launch shape to direction `which` of the schedule."""
     if c["exec"] == "blocks":
         sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
+        sched.set_split(which, 0)
     else:
         c["part_cost_target"] = max(1, c["items"] * mean)
         sched.recut(which, c["part_cost_target"], c["lanes"], c["team"])
         sched.reblock(which, 0, 1, 0)
+        sched.set_split(which, c.get("split", 0))
 
 
 def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype: torch.dtype = torch.float64,
          k: int = 1, lanes: Sequence[int] = DEFAULT_LANES, items: Sequence[int] = DEFAULT_ITEMS,
          teams: Sequence[int] = DEFAULT_TEAMS, blocks: bool = True,
          block_rows: Sequence[int] = DEFAULT_BLOCK_ROWS, block_lanes: Sequence[int] = DEFAULT_BLOCK_LANES,
-         reps: int = 3, budget_s: float = 20.0, use_cache: bool = True) -> Dict:
+         splits: Sequence[int] = DEFAULT_SPLITS, reps: int = 3, budget_s: float = 20.0,
+         use_cache: bool = True) -> Dict:
     """Chooses the executor and its launch shape for `which` (0 forward, 1 adjoint) of
     `sched`, timing `run()` (one execution) for every candidate within `budget_s` seconds.
     Leaves the schedule set to the best candidate and returns it as a dict (exec, its
@@ -138,6 +143,19 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
         trials.append(dict(c, ms=ms))
         if best is None or ms < best["ms"]:
             best = trials[-1]
+    # separated schedules: the best partition shape with the teams split between the solve
+    # chain and the second-kernel rows
+    if best is not None and best["exec"] == "partitions" and splits and \
+            inf["parts_class0" if which == 0 else "adj_parts_class0"] > 0:
+        for pct in splits:
+            c = {k: v for k, v in best.items() if k in ("exec", "lanes", "items", "team")}
+            c["split"] = pct
+            _apply(sched, which, c, mean)
+            ms = _time(run, reps)
+            sched.check()
+            trials.append(dict(c, ms=ms))
+            if ms < best["ms"]:
+                best = trials[-1]
     _apply(sched, which, best, mean)
     if use_cache:
         cache = _load_cache(path)

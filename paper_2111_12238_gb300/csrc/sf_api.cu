@@ -65,6 +65,9 @@ struct Dir {
     long long W = 0;            // items of cost > W run on a whole warp (0: none)
     int lpr = 1;                // lanes per row of this direction's launches
     int team = 8;               // lanes of a team (the unit that runs a partition)
+    int *plist = nullptr;       // separated kinds: class-0 then class-1 partitions
+    int n_parts0 = 0;           // class-0 partitions (first vertex in the first kernel)
+    int split_pct = 0;          // percent of teams that run class 0 (0: one class for all)
     int *cost = nullptr;        // c(v) of every vertex (kept for re-cutting)
     long long cost_total = 0;
     // row-block schedule (k = 1 executor with shared-memory dependences)
@@ -203,6 +206,14 @@ sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Aren
     d.W = d.lpr < 32 ? 16LL * d.lpr + 1 : 0;
     e = cut_partitions(nv, Sx, cs, C, d.W, d.part_ptr, d.part_wide, &d.n_parts, s, tmp);
     if (e != cudaSuccess) return from_cuda(e, "partition cut");
+    if (d.kind == K_SEP || d.kind == K_SEP_T) {
+        if (!d.plist) {
+            d.plist = (int *)S->keep.alloc(sizeof(int) * ((size_t)nv + 1));
+            if (!d.plist) return fail(SF_ERR_OOM, "inspector: out of device memory");
+        }
+        e = split_partition_classes(d.n_parts, d.part_ptr, d.order, d.plist, &d.n_parts0, s, tmp);
+        if (e != cudaSuccess) return from_cuda(e, "partition classes");
+    }
     return SF_OK;
 }
 
@@ -491,13 +502,28 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         }
         return fail(SF_ERR_UNSUPPORTED, "row blocks of %d rows do not fit in shared memory", d.B);
     }
-    if (vf) SF_CK(cudaMemsetAsync(vbuf, 0xff, (size_t)S->n * (dt == SF_F64 ? 8 : 4), s), "value-flag reset");
+    if (vf) {
+        // value-flag reset and reciprocal diagonals in one pass
+        a.rdiag = d.aux;
+        SF_CK(launch_rdiag(dtype, S->n, S->L.rowptr, a.Lv, vbuf, d.aux, d.st, s), "value-flag reset");
+    }
     int per_sm = occupancy(mode, dtype, lpr, vf, team);
     if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
     long long blocks = (long long)per_sm * S->sms;
     const long long teams_per_block = 8LL * (32 / team);
     blocks = std::min<long long>(blocks, ((long long)d.n_parts + teams_per_block - 1) / teams_per_block);
     blocks = std::max<long long>(blocks, 1);
+    // two partition classes when a split is set: split_pct percent of the teams run the
+    // partitions that open with a first-kernel row, the others the second-kernel ones
+    const long long nteams = blocks * teams_per_block;
+    a.plist = nullptr;
+    if (d.split_pct > 0 && d.plist && d.n_parts0 > 0 && d.n_parts0 < d.n_parts && nteams >= 2 &&
+        !S->dynamic_queue) {
+        a.plist = d.plist;
+        a.n_parts0 = d.n_parts0;
+        const long long t0 = (nteams * d.split_pct + 50) / 100;
+        a.teams0 = (int)std::min<long long>(std::max<long long>(t0, 1), nteams - 1);
+    }
     cudaError_t e;
     if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, team, (int)blocks, s, a);
     else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
@@ -837,6 +863,10 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     info->adj_exec_mode = S->adj.exec_mode;
     info->block_lanes = S->fwd.blpr;
     info->adj_block_lanes = S->adj.blpr;
+    info->parts_class0 = S->fwd.n_parts0;
+    info->adj_parts_class0 = S->adj.n_parts0;
+    info->split_pct = S->fwd.split_pct;
+    info->adj_split_pct = S->adj.split_pct;
     info->block_segments = S->fwd.n_segs;
     info->adj_block_segments = S->adj.n_segs;
     info->block_threads = S->fwd.present ? block_threads(S->fwd) : 0;
@@ -937,6 +967,17 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
         if (lanes_per_row) dirs[w]->blpr = lanes_per_row;
     }
     SF_CK(cudaStreamSynchronize(s), "reblock");
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_split(sf_schedule *S, int32_t which, int32_t class0_pct) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (class0_pct < 0 || class0_pct > 99) return fail(SF_ERR_INVALID_ARG, "class0_pct must be in [0, 99]");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w)
+        if ((which == -1 || which == w) && dirs[w]->present) dirs[w]->split_pct = class0_pct;
     return SF_OK;
 }
 

@@ -34,7 +34,15 @@
 namespace sf {
 
 constexpr int kUnroll = 4;   // row entries fetched per lane before waiting on them
-constexpr unsigned kBackoffMinNs = 20, kBackoffMaxNs = 256;
+#ifndef SF_BACKOFF_MIN_NS
+#define SF_BACKOFF_MIN_NS 20
+#endif
+#ifndef SF_BACKOFF_MAX_NS
+#define SF_BACKOFF_MAX_NS 64
+#endif
+// Sleep between polls of a dependence: doubles from the minimum to the maximum (build-time
+// constants; shorter sleeps see a published value sooner but load L2 with more polls).
+constexpr unsigned kBackoffMinNs = SF_BACKOFF_MIN_NS, kBackoffMaxNs = SF_BACKOFF_MAX_NS;
 
 // ------------------------------------------------------------------ value-flag helpers
 template <typename T> __device__ __forceinline__ T ld_relaxed_val(const T *p);
@@ -242,6 +250,19 @@ __device__ __forceinline__ void store_out(T *p, T v) {
     else *p = v;
 }
 
+// Diagonal of a solve row. With a reciprocal table (a.rdiag: 1 / L_ii written by the pre-pass
+// of k = 1 launches with value flags) the row finishes with a multiply, which takes the
+// division off the dependence chain; the table's pre-pass also checks for zero diagonals.
+template <typename T>
+__device__ __forceinline__ T load_diag(const ExecArgs &a, const T *vals, int e, int row, int gl) {
+    if (a.rdiag) return __ldg((const T *)a.rdiag + row);
+    const T d = __ldg(vals + e);
+    if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, row);
+    return d;
+}
+template <typename T>
+__device__ __forceinline__ T finish_row(const ExecArgs &a, T num, T d) { return a.rdiag ? num * d : num / d; }
+
 // ---------------------------------------------------------------- item kinds
 // SpTRSV row (Table 2, forward substitution): x_i = (b_i - sum_{j<i} L_ij x_j) / L_ii.
 // `x` is both the output and the buffer the dependences are read from.
@@ -250,16 +271,17 @@ __device__ bool item_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, un
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Lv = (const T *)a.Lv, *b = (const T *)a.b;
-    const T d = __ldg(Lv + dg);
-    if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, row);
+    const T d = load_diag<T>(a, Lv, dg, row, gl);
     bool ok = true;
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
+        // operands that need no wait are loaded before it, off the dependence chain
+        const T bc = (s == 0 && act) ? __ldg(b + (size_t)row * k + c) : T(0);
         T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Lci, nullptr, Lv, rs + s, dg, S, x, k, c, act, a.flags,
                                                          epoch, a.st, a.timeout_ns, row, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
-        if (s == 0 && act) store_out<VF>(x + (size_t)row * k + c, (__ldg(b + (size_t)row * k + c) - acc) / d);
+        if (s == 0 && act) store_out<VF>(x + (size_t)row * k + c, finish_row<T>(a, bc - acc, d));
     }
     ok = group_ok<LPR>(ok, gmask);
     if (!VF) publish(a, row, epoch, gl, gmask, ok);
@@ -295,22 +317,20 @@ __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int g
     const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Lv = (const T *)a.Lv, *b = (const T *)a.b;
     T *z = (T *)a.y;
-    const T d = __ldg(Lv + dg);
-    if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, row);
+    const T d = load_diag<T>(a, Lv, dg, row, gl);
     bool ok = true;
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
+        const T bc = (s == 0 && act) ? __ldg(b + (size_t)row * k + c) : T(0);
         T accA = row_dot<T, D_NONE, false>(a.Mci, nullptr, (const T *)a.Mv, ra + s, re, S, (const T *)a.xin, k, c,
                                            act, a.flags, epoch, a.st, a.timeout_ns, row, ok);
+        accA = slice_sum<LPR>(accA, kt, gmask);
+        const T r = bc - accA;   // r_i is complete before the wait on z
         T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Lci, nullptr, Lv, rs + s, dg, S, z, k, c, act, a.flags,
                                                           epoch, a.st, a.timeout_ns, row, ok);
-        accA = slice_sum<LPR>(accA, kt, gmask);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        if (s == 0 && act) {
-            const T r = __ldg(b + (size_t)row * k + c) - accA;
-            store_out<VF>(z + (size_t)row * k + c, (r - accL) / d);
-        }
+        if (s == 0 && act) store_out<VF>(z + (size_t)row * k + c, finish_row<T>(a, r - accL, d));
     }
     ok = group_ok<LPR>(ok, gmask);
     if (!VF) publish(a, row, epoch, gl, gmask, ok);
@@ -395,19 +415,18 @@ __device__ bool item_adj_trsv_spmv(const ExecArgs &a, int j, unsigned epoch, int
     const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);   // first entry of L^T row j is L_jj
     const T *LTv = (const T *)a.LTv, *gy = (const T *)a.gy;
     T *lam = (T *)a.gb;
-    const T d = __ldg(LTv + ls);
-    if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, j);
+    const T d = load_diag<T>(a, LTv, ls, j, gl);
     bool ok = true;
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
         T u = row_dot<T, D_NONE, false>(a.MTci, nullptr, (const T *)a.MTv, ms + s, me, S, gy, k, c, act, a.flags,
                                         epoch, a.st, a.timeout_ns, j, ok);
+        u = slice_sum<LPR>(u, kt, gmask);   // u_j is complete before the wait on lam
         T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
                                                           a.flags, epoch, a.st, a.timeout_ns, j, ok);
-        u = slice_sum<LPR>(u, kt, gmask);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, (u - accL) / d);
+        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, finish_row<T>(a, u - accL, d));
     }
     ok = group_ok<LPR>(ok, gmask);
     if (!VF) publish(a, j, epoch, gl, gmask, ok);
@@ -421,16 +440,16 @@ __device__ bool item_adj_lam(const ExecArgs &a, int j, unsigned epoch, int gl, i
     const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);
     const T *LTv = (const T *)a.LTv, *gz = (const T *)a.gy;
     T *lam = (T *)a.gb;
-    const T d = __ldg(LTv + ls);
-    if (gl == 0 && d == T(0)) record_error(a.st, SF_ERR_NONFINITE, j);
+    const T d = load_diag<T>(a, LTv, ls, j, gl);
     bool ok = true;
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
+        const T gc = (s == 0 && act) ? __ldg(gz + (size_t)j * k + c) : T(0);
         T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
                                                           a.flags, epoch, a.st, a.timeout_ns, j, ok);
         accL = slice_sum<LPR>(accL, kt, gmask);
-        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, (__ldg(gz + (size_t)j * k + c) - accL) / d);
+        if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, finish_row<T>(a, gc - accL, d));
     }
     ok = group_ok<LPR>(ok, gmask);
     if (!VF) publish(a, j, epoch, gl, gmask, ok);
@@ -485,6 +504,7 @@ __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, un
 }
 
 constexpr int kExecThreads = 256;
+
 #ifndef SF_MIN_BLOCKS
 #define SF_MIN_BLOCKS 1
 #endif
@@ -514,9 +534,25 @@ __global__ void __launch_bounds__(kExecThreads, SF_MIN_BLOCKS) k_exec(const Exec
     const int team = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NT + lane / TEAM;
     bool ok = true;
     // A team holds its current partition (and with tickets the ticket of its next one);
-    // every team runs its partitions in increasing order, so the smallest unfinished
-    // partition is always being run by a team whose dependences are all finished.
-    int p = a.dynamic ? __shfl_sync(tmask, draw_ticket(a, tl), tbase) : team;
+    // every team runs its partitions in increasing order (within its class), so the smallest
+    // unfinished partition is always being run by a team whose dependences are all finished.
+    // With two classes (separated schedules) teams [0, teams0) run the class-0 list and the
+    // others the class-1 list, each round robin in increasing order; second-kernel rows then
+    // never hold up a team that the dependence chain is waiting for.
+    int idx = team, stride = nteams, base = 0, end = a.n_parts;
+    if (!a.dynamic && a.plist) {
+        if (team < a.teams0) {
+            stride = a.teams0;
+            end = a.n_parts0;
+        } else {
+            idx = team - a.teams0;
+            stride = nteams - a.teams0;
+            base = a.n_parts0;
+            end = a.n_parts - a.n_parts0;
+        }
+    }
+    auto part_at = [&](int i) { return i < end ? (a.plist ? __ldg(a.plist + base + i) : base + i) : a.n_parts; };
+    int p = a.dynamic ? __shfl_sync(tmask, draw_ticket(a, tl), tbase) : part_at(idx);
     while (p < a.n_parts) {
         const int pn_first = a.dynamic ? draw_ticket(a, tl) : 0;
         const int q0 = __ldg(a.part_ptr + p), q1 = __ldg(a.part_ptr + p + 1);
@@ -533,7 +569,10 @@ __global__ void __launch_bounds__(kExecThreads, SF_MIN_BLOCKS) k_exec(const Exec
         }
         if (!__all_sync(tmask, ok)) break;
         if (a.dynamic) p = __shfl_sync(tmask, pn_first, tbase);
-        else p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : p + nteams;
+        else {
+            idx += stride;
+            p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : part_at(idx);
+        }
     }
     __syncwarp();
     if (lane == 0) {

@@ -16,6 +16,28 @@ const void *block_kernel(int mode, int dtype, int lpr) {
 
 }  // namespace
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_rdiag(int n, const int *__restrict__ Lrp, const T *__restrict__ Lv, T *vec,
+                                               T *__restrict__ rdiag, ExecState *st) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)t;
+        vec[i] = unset_value<T>();
+        const T d = Lv[__ldg(Lrp + i + 1) - 1];
+        if (d == T(0)) record_error(st, SF_ERR_NONFINITE, i);
+        rdiag[i] = T(1) / d;
+    }
+}
+
+cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void *vec, void *rdiag, ExecState *st,
+                         cudaStream_t s) {
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(((long long)n + 255) / 256, 65535LL));
+    if (dtype == 0)
+        k_rdiag<double><<<grid, 256, 0, s>>>(n, Lrp, (const double *)Lv, (double *)vec, (double *)rdiag, st);
+    else
+        k_rdiag<float><<<grid, 256, 0, s>>>(n, Lrp, (const float *)Lv, (float *)vec, (float *)rdiag, st);
+    return cudaGetLastError();
+}
+
 size_t block_exec_smem(int mode, int dtype, int block_rows) {
     (void)mode;
     return (size_t)block_rows * (dtype == 0 ? 8 : 4);

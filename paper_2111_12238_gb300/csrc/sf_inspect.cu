@@ -612,6 +612,34 @@ cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs
     return cudaStreamSynchronize(s);
 }
 
+// Partition classes of a separated schedule: class 1 when the partition's first vertex is a
+// second-kernel row (a sink of the joint DAG), else class 0. plist lists the class-0
+// partitions in increasing order, then the class-1 partitions in increasing order.
+__global__ void k_part_class(int P, const int *__restrict__ part_ptr, const int *__restrict__ order, int *__restrict__ f0) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+        f0[p] = ((unsigned)order[part_ptr[p]] >> 31) ? 0 : 1;
+}
+
+__global__ void k_part_list(int P, const int *__restrict__ f0, const int *__restrict__ pos0, int *__restrict__ plist) {
+    const int P0 = pos0[P];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+        plist[f0[p] ? pos0[p] : P0 + (p - pos0[p])] = p;
+}
+
+cudaError_t split_partition_classes(int P, const int *part_ptr, const int *order, int *plist, int *n_class0,
+                                    cudaStream_t s, Arena &ar) {
+    int *f0 = (int *)ar.alloc(sizeof(int) * ((size_t)P + 1));
+    int *pos0 = (int *)ar.alloc(sizeof(int) * ((size_t)P + 1));
+    if (!f0 || !pos0) return cudaErrorMemoryAllocation;
+    k_part_class<<<grid_for(P, 256, 4096), 256, 0, s>>>(P, part_ptr, order, f0);
+    cudaError_t e = scan_excl<int>(f0, pos0, P, s, ar);
+    if (e != cudaSuccess) return e;
+    k_part_list<<<grid_for(P, 256, 4096), 256, 0, s>>>(P, f0, pos0, plist);
+    e = cudaMemcpyAsync(n_class0, pos0 + P, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
 // ------------------------------------------------------------------------------ row blocks
 // Block of every vertex for the row-block executor: first-kernel rows by their own row
 // (decreasing row order for the transposed kinds), second-kernel rows by the latest block

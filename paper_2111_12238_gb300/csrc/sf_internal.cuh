@@ -53,6 +53,9 @@ struct ExecArgs {
     int k;
     int kt;                 // right-hand-side columns handled side by side (pow2 <= lanes)
     int dynamic;            // 1: partitions from a ticket counter; 0: static round robin
+    const int *plist;       // static: class-0 then class-1 partitions (NULL: one class)
+    int n_parts0;           // class-0 partitions in plist
+    int teams0;             // teams that run class 0; the others run class 1
     const int *block_ptr;   // row-block executor: first position of each block in `order`
     const int2 *bdesc;      // row-block executor: entry range of the row each position waits on
     const int *seg_ptr;     // row-block executor: level segments of `order`
@@ -71,6 +74,7 @@ struct ExecArgs {
     const void *LTv, *MTv;              // values of L^T and M^T / A^T in transposed order (adjoint)
     void *y, *xs, *gb, *gx, *gL, *gM;
     void *aux;                          // row-block executor: (c_i, 1 / L_ii) per row
+    const void *rdiag;                  // 1 / L_ii per row (k = 1 value-flag launches), or NULL
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
@@ -88,6 +92,10 @@ cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int thre
                               const ExecArgs &a);
 int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threads);
 size_t block_exec_smem(int mode, int dtype, int block_rows);
+// Pre-pass of partition launches with value flags: resets vec[0..n) to the all-ones pattern
+// and writes rdiag[i] = 1 / L_ii (L's diagonal is the last entry of each row).
+cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void *vec, void *rdiag, ExecState *st,
+                         cudaStream_t s);
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team);
 int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team);

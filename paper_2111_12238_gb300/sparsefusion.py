@@ -56,7 +56,9 @@ class SfInfo(C.Structure):
                 ("adj_n_blocks", C.c_int32), ("exec_mode", C.c_int32), ("adj_exec_mode", C.c_int32),
                 ("block_lanes", C.c_int32), ("adj_block_lanes", C.c_int32),
                 ("block_segments", C.c_int32), ("adj_block_segments", C.c_int32),
-                ("block_threads", C.c_int32), ("adj_block_threads", C.c_int32)]
+                ("block_threads", C.c_int32), ("adj_block_threads", C.c_int32),
+                ("parts_class0", C.c_int32), ("adj_parts_class0", C.c_int32),
+                ("split_pct", C.c_int32), ("adj_split_pct", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -87,6 +89,7 @@ _SIGS = {
     "sf_schedule_recut": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, _P]),
     "sf_schedule_reblock": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
     "sf_schedule_export_blocks": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "sf_schedule_set_split": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
@@ -289,6 +292,12 @@ class Schedule:
                "sf_schedule_export_blocks")
         return dict(order=order, block_ptr=bp, seg_ptr=sp, block_seg=bs,
                     block_rows=inf["block_rows"] if which == 0 else inf["adj_block_rows"])
+
+    def set_split(self, which=-1, class0_pct=0):
+        """Runs the partitions that open with a first-kernel row on class0_pct percent of the
+        teams (separated schedules; 0 = one class)."""
+        _check(load_library().sf_schedule_set_split(self.handle, int(which), int(class0_pct)),
+               "sf_schedule_set_split")
 
     def set_timeout(self, ns: int):
         _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")

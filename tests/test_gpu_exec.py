@@ -281,3 +281,34 @@ def test_team_widths(team, lpr):
     assert col_rel_err(host(y), y_ref) < 1e-12
     assert col_rel_err(host(gb), gb_ref) < 1e-12
     assert vec_rel_err(host(gL), gL_ref) < 1e-12 and vec_rel_err(host(gM), gM_ref) < 1e-12
+
+
+@pytest.mark.parametrize("pct", [0, 10, 50, 90, 99])
+def test_partition_class_split_is_exact(pct):
+    # separated schedules with the teams split between the partitions that open with a
+    # first-kernel row and the others: forward SpTRSV -> SpMV and the SpMV -> SpTRSV adjoint
+    need_cuda()
+    w = _lap3d(12, 1)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), part_cost_target=9)
+    sch.set_split(0, pct)
+    inf = sch.info()
+    assert inf["split_pct"] == pct and 0 < inf["parts_class0"] < inf["n_parts"]
+    Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
+    xs = torch.empty_like(b)
+    for _ in range(2):
+        y = sch.execute(Lv, Mv, b=b, x_save=xs)
+        sch.check()
+        assert col_rel_err(host(xs), x_ref) < 1e-12 and col_rel_err(host(y), y_ref) < 1e-12
+    p = I.spmv_trsv_powerlaw(n=6000, k=1, mean=10, lmax=80, halfband=400, seed=41)
+    z_ref = oracle.spmv_trsv(p.M, p.L, p.x_in, p.b)
+    gb_ref, gx_ref, _, _ = oracle.adj_spmv_trsv(p.M, p.L, p.x_in, z_ref, p.gy)
+    s2 = sf.inspect("spmv_trsv", dev_csr(p.L), dev_csr(p.M), want_adjoint=True, part_cost_target=12)
+    s2.set_split(1, pct)
+    assert s2.info()["adj_split_pct"] == pct
+    Lv2, Av, xin = t(p.L.vals), t(p.M.vals), t(p.x_in)
+    z = s2.execute(Lv2, Av, b=t(p.b), x_in=xin)
+    gx = torch.empty_like(xin)
+    gb = s2.adjoint(Lv2, Av, t(p.gy), saved=z, x_in=xin, gx=gx)
+    s2.check()
+    assert col_rel_err(host(gb), gb_ref) < 1e-12 and col_rel_err(host(gx), gx_ref) < 1e-12

@@ -58,6 +58,10 @@ def test_schedule_matches_oracle(wname, pair, target):
         assert np.array_equal(got["part_ptr"], ref["part_ptr"])
         assert oracle.validate(kind, L, M if kind in (oracle.SEP, oracle.SEP_T) else None,
                                got["order"], got["part_ptr"]) == 0
+        # partition classes of separated schedules: partitions that open with a first-kernel row
+        first = ref["order"].view(np.uint32)[ref["part_ptr"][:-1]] >> 31
+        n0 = int((first == 0).sum()) if kind in (oracle.SEP, oracle.SEP_T) else 0
+        assert info["parts_class0" if which == 0 else "adj_parts_class0"] == n0
 
 
 def test_grid_levels_closed_form_on_gpu():

@@ -102,17 +102,21 @@ def make_workload(name, dtype_name):
     if w.pair == "trsv_spmv":
         fwd_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec      # b in, x and y out
         adj_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec + es * (nnzL + nnzM)
+        # fused adjoint kernel alone: L^T and M^T (pattern, values), gy in, lam out
+        adj_exec_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 2 * vec
         fwd_flops = 2 * (nnzL + nnzM) * k
     elif w.pair == "spmv_trsv":
         fwd_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec      # x_in, b in, z out
         adj_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 5 * vec + es * (nnzL + nnzM)
+        # fused adjoint kernel alone: L^T and A^T (pattern, values), gz in, lam and gx out
+        adj_exec_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec
         fwd_flops = 2 * (nnzL + nnzM) * k
     else:  # ic0_trsv: read tril(A) values + pattern, write factor values, b in, y out
         fwd_bytes = csr_bytes(nnzL, n, es) + es * nnzL + 2 * vec
-        adj_bytes = 0
+        adj_bytes = adj_exec_bytes = 0
         fwd_flops = 2 * nnzL * k + 4 * nnzL
     return dict(w=w, name=name, pair=w.pair, n=n, k=k, nnzL=nnzL, nnzM=nnzM, adj=adj, es=es,
-                fwd_bytes=fwd_bytes, adj_bytes=adj_bytes, fwd_flops=fwd_flops,
+                fwd_bytes=fwd_bytes, adj_bytes=adj_bytes, adj_exec_bytes=adj_exec_bytes, fwd_flops=fwd_flops,
                 fits_l2=(fwd_bytes < 129e6))
 
 
@@ -209,14 +213,17 @@ class Gpu:
         self.un_sched.check()
 
 
-def _time_loop(torch, fns, steps, flush=None):
+def _time_loop(torch, fns, steps, flush=None, before=None):
     """Runs `steps` iterations of the launches in `fns` on the current stream with CUDA
-    events around each launch; returns (total_ms, [per-fn total ms])."""
+    events around each launch; returns (total_ms, [per-fn total ms]). before(s), when
+    given, runs on the host before step s is enqueued."""
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(steps)]
     torch.cuda.synchronize()
     for s in range(steps):
         if flush is not None:
             flush()
+        if before is not None:
+            before(s)
         ev[s][0].record()
         for i, f in enumerate(fns):
             f()
@@ -353,12 +360,29 @@ def run_gpu(args):
         args.steps = int(min(2000, max(20, 3000.0 / max(one / 3, 1e-3))))
 
     # ---- timed region (device-resident inputs)
+    # the fused executor kernel of each pass is also timed alone: the library records a pair
+    # of these events around it on the launch stream (sf_schedule_set_exec_events)
+    dirs = [0] + ([1] if wl["adj"] else [])
+    kev = {w: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)] for w in dirs}
+    for pairs in kev.values():
+        for a_, b_ in pairs:
+            a_.record()
+            b_.record()
+
+    def before(s):
+        for w in dirs:
+            g.sched.set_exec_events(w, *kev[w][s])
+
     clk = ClockSampler(_gpu_id(torch, local))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    total_ms, per = _time_loop(torch, fns, args.steps, flush)
+    total_ms, per = _time_loop(torch, fns, args.steps, flush, before)
     clocks = clk.stop()
+    for w in dirs:
+        g.sched.set_exec_events(w, None, None)
+    exec_ms = {w: sum(a_.elapsed_time(b_) for a_, b_ in kev[w]) / args.steps for w in dirs}
     g.check()
     if world > 1:
         t = torch.tensor([total_ms], device=device)
@@ -414,9 +438,11 @@ def run_gpu(args):
         return
     hbm, peak_src = _peaks()
     info = g.sched.info()
-    dom = "fwd" if (adj_ms is None or fwd_ms >= adj_ms) else "adj"
-    dom_ms = fwd_ms if dom == "fwd" else adj_ms
-    dom_bytes = wl["fwd_bytes"] if dom == "fwd" else wl["adj_bytes"]
+    pre = int(wl["k"] == 1 and wl["pair"] != "ic0_trsv")   # pre-pass of value-flag launches
+    # dominant kernel: the longer of the fused forward and fused adjoint executor kernels
+    dom = "fwd" if (1 not in exec_ms or exec_ms[0] >= exec_ms[1]) else "adj"
+    dom_ms = exec_ms[0] if dom == "fwd" else exec_ms[1]
+    dom_bytes = wl["fwd_bytes"] if dom == "fwd" else wl["adj_exec_bytes"]
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     traffic = _recorded_traffic(args.workload, dom)
     thop = t_hop_ns(torch, device)
@@ -445,8 +471,10 @@ def run_gpu(args):
             "instances": len(wl["w"].instances) or 1,
         },
         "roofline": {
-            "kernel": "fused forward k_exec (one launch)" if dom == "fwd" else
-                      "sf_adjoint (value gathers, fused k_exec pass, gradient passes)",
+            "kernel": ("fused forward executor kernel" if dom == "fwd" else "fused adjoint executor kernel") +
+                      (" (row blocks)" if info["exec_mode" if dom == "fwd" else "adj_exec_mode"] == 2
+                       else " (partitions)"),
+            "kernel_ms": dom_ms,
             "bound": "hbm",
             "achieved": achieved,
             "peak": hbm,
@@ -460,6 +488,8 @@ def run_gpu(args):
         },
         "fwd_ms": fwd_ms,
         "adj_ms": adj_ms,
+        "fwd_exec_ms": exec_ms[0],
+        "adj_exec_ms": exec_ms.get(1),
         "adjoint_fwd_ratio": (adj_ms / fwd_ms) if adj_ms else None,
         "fwd_solves_per_s": 1e3 / fwd_ms,
         "fwd_gbs": wl["fwd_bytes"] / (fwd_ms / 1e3) / 1e9,
@@ -476,9 +506,10 @@ def run_gpu(args):
         "tuned": tuned,
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        # one fused launch per forward; per adjoint two value gathers, the fused pass and up to
-        # two gradient passes
-        "gpu_launches": args.steps * (1 + (5 if wl["adj"] else 0)),
+        # per forward: the pre-pass (value-flag reset and 1 / L_ii, one right-hand side only)
+        # and the fused kernel; per adjoint: two value gathers, the pre-pass, the fused kernel
+        # and two gradient passes
+        "gpu_launches": args.steps * ((1 + pre) + ((5 + pre) if wl["adj"] else 0)),
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -249,6 +249,13 @@ sf_status sf_schedule_recut(sf_schedule *sch, int32_t which, int64_t part_cost_t
 sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,
                               int32_t lanes_per_row, void *stream);
 
+/* Timing hook: the next launches of the forward (0) or adjoint (1) schedule record ev_start
+ * (a cudaEvent_t) on the launch stream right before the fused executor kernel and ev_stop
+ * right after it (pre-passes, gathers and gradient passes fall outside), so a caller can
+ * time the executor kernel alone with cudaEventElapsedTime. Both NULL stops the recording.
+ * The events stay owned by the caller and must outlive the launches. No GPU work. */
+sf_status sf_schedule_set_exec_events(sf_schedule *sch, int32_t which, void *ev_start, void *ev_stop);
+
 /* Partition classes of the separated schedules (SpTRSV -> SpMV forward, SpMV -> SpTRSV
  * adjoint): with class0_pct in 1..99 that percent of the executor's teams run the partitions
  * whose first vertex is a first-kernel row (the solve chain), the other teams run the

@@ -68,6 +68,7 @@ struct Dir {
     int *plist = nullptr;       // separated kinds: class-0 then class-1 partitions
     int n_parts0 = 0;           // class-0 partitions (first vertex in the first kernel)
     int split_pct = 0;          // percent of teams that run class 0 (0: one class for all)
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // recorded around the executor kernel
     int *cost = nullptr;        // c(v) of every vertex (kept for re-cutting)
     long long cost_total = 0;
     // row-block schedule (k = 1 executor with shared-memory dependences)
@@ -496,7 +497,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
             if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
             long long blocks = std::min<long long>((long long)per_sm * S->sms, d.nb);
             blocks = std::max<long long>(blocks, 1);
-            cudaError_t e = launch_block_exec(mode, dtype, d.blpr, (int)blocks, threads, s, a);
+            cudaError_t e = launch_block_exec(mode, dtype, d.blpr, (int)blocks, threads, s, a, d.ev_start, d.ev_stop);
             if (e != cudaSuccess) return from_cuda(e, "row-block executor launch");
             return SF_OK;
         }
@@ -525,11 +526,13 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         a.teams0 = (int)std::min<long long>(std::max<long long>(t0, 1), nteams - 1);
     }
     cudaError_t e;
+    if (d.ev_start) SF_CK(cudaEventRecord(d.ev_start, s), "timing event");
     if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, team, (int)blocks, s, a);
     else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
         e = launch_exec_adj(mode, dtype, lpr, vf, team, (int)blocks, s, a);
     else e = launch_exec_pair(mode, dtype, lpr, vf, team, (int)blocks, s, a);
     if (e != cudaSuccess) return from_cuda(e, "executor launch");
+    if (d.ev_stop) SF_CK(cudaEventRecord(d.ev_stop, s), "timing event");
     return SF_OK;
 }
 
@@ -967,6 +970,17 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
         if (lanes_per_row) dirs[w]->blpr = lanes_per_row;
     }
     SF_CK(cudaStreamSynchronize(s), "reblock");
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_exec_events(sf_schedule *S, int32_t which, void *ev_start, void *ev_stop) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which != 0 && which != 1) return fail(SF_ERR_INVALID_ARG, "which must be 0 or 1");
+    if ((ev_start == nullptr) != (ev_stop == nullptr)) return fail(SF_ERR_INVALID_ARG, "set both events or neither");
+    Dir &d = which ? S->adj : S->fwd;
+    if (!d.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    d.ev_start = (cudaEvent_t)ev_start;
+    d.ev_stop = (cudaEvent_t)ev_stop;
     return SF_OK;
 }
 

@@ -60,7 +60,7 @@ int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threa
 }
 
 cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int threads, cudaStream_t s,
-                              const ExecArgs &a) {
+                              const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
     const void *prep = block_kernel(mode, dtype, 0);
     const void *f = lpr ? block_kernel(mode, dtype, lpr) : nullptr;
     if (!prep || !f || threads < 32 || threads > kBlockMaxThreads || threads % 32) return cudaErrorInvalidValue;
@@ -72,7 +72,10 @@ cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int thre
     const size_t smem = block_exec_smem(mode, dtype, std::min(a.block_rows, a.n));
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(threads), args, smem, s);
+    if (ev_start && (e = cudaEventRecord(ev_start, s)) != cudaSuccess) return e;
+    e = cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(threads), args, smem, s);
+    if (e != cudaSuccess) return e;
+    return ev_stop ? cudaEventRecord(ev_stop, s) : cudaSuccess;
 }
 
 }  // namespace sf

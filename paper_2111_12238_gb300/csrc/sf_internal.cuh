@@ -89,7 +89,7 @@ cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int team, int
 // `threads` threads per CTA (a multiple of 32, at most kBlockMaxThreads).
 constexpr int kBlockMaxThreads = 512;
 cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int threads, cudaStream_t s,
-                              const ExecArgs &a);
+                              const ExecArgs &a, cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threads);
 size_t block_exec_smem(int mode, int dtype, int block_rows);
 // Pre-pass of partition launches with value flags: resets vec[0..n) to the all-ones pattern

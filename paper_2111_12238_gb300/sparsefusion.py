@@ -90,6 +90,7 @@ _SIGS = {
     "sf_schedule_reblock": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
     "sf_schedule_export_blocks": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "sf_schedule_set_split": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_set_exec_events": (C.c_int, [_P, C.c_int32, _P, _P]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
@@ -292,6 +293,16 @@ class Schedule:
                "sf_schedule_export_blocks")
         return dict(order=order, block_ptr=bp, seg_ptr=sp, block_seg=bs,
                     block_rows=inf["block_rows"] if which == 0 else inf["adj_block_rows"])
+
+    def set_exec_events(self, which, start=None, stop=None):
+        """Records torch.cuda.Event pair (start, stop) around the next launches of the fused
+        executor kernel of direction `which`; None, None stops recording."""
+        hs = int(start.cuda_event) if start is not None else 0
+        he = int(stop.cuda_event) if stop is not None else 0
+        if (start is not None) and (hs == 0 or he == 0):
+            raise ValueError("record each event once before passing it (torch creates events lazily)")
+        _check(load_library().sf_schedule_set_exec_events(self.handle, int(which), hs or None, he or None),
+               "sf_schedule_set_exec_events")
 
     def set_split(self, which=-1, class0_pct=0):
         """Runs the partitions that open with a first-kernel row on class0_pct percent of the

@@ -257,7 +257,9 @@ def n_vertices(kind, n):
     return 2 * n if kind in (SEP, SEP_T) else n
 
 
-def levels(kind, L, M=None):
+def levels(kind, L, M=None, g2=0):
+    """Wavefront of every joint-DAG vertex; g2 places the second kernel's vertices of a
+    separated schedule (0 earliest, -1 last wavefront, d > 0 delayed by d)."""
     lib = _load()
     n = L.n_rows
     kl, lrp, lci, _ = _csr(L)
@@ -267,6 +269,8 @@ def levels(kind, L, M=None):
         mrp = mci = None
     lev, pl = _out(n_vertices(kind, n), np.int32)
     _check(lib.orc_levels(C.c_int32(kind), C.c_int32(n), lrp, lci, mrp, mci, pl), "levels")
+    if g2:
+        lib.orc_place_g2(C.c_int32(kind), C.c_int32(n), pl, C.c_int32(int(g2)))
     return lev
 
 
@@ -354,10 +358,10 @@ def validate(kind, L, M, order_, part_ptr):
                             ppp, C.c_int64(len(pp) - 1))
 
 
-def schedule(kind, what, L, M, target, wide=0):
+def schedule(kind, what, L, M, target, wide=0, g2=0):
     """Levels, order and partition pointers of one schedule, as the inspector must build
     them: returns dict(level, order, part_ptr, depth, cost)."""
-    lev = levels(kind, L, M)
+    lev = levels(kind, L, M, g2)
     o, depth = order(lev, L.n_rows)
     c = costs(what, L, M)
     pp = partition(o, L.n_rows, c, target, wide)

@@ -333,6 +333,24 @@ int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, c
 /* Linearised order of the joint DAG: vertices sorted by (level, tag, row), the canonical
  * tie-break among the many valid topological orders. Vertex v = tag*n + row is encoded as
  * row | tag << 31. Counting sort by level over vertices in increasing v. */
+/* Placement of the second kernel's vertices in a separated schedule (kinds 0 and 3), using
+ * their slack (§3.2.2): such a vertex (an SpMV row, or an A^T row of the adjoint) is a sink of
+ * the joint DAG, so any wavefront from its earliest one (the longest-path level) to the last
+ * one, depth - 1, keeps every edge pointing forward. mode 0 keeps the earliest wavefront,
+ * mode < 0 moves every such vertex to the last wavefront (as late as possible), mode d > 0
+ * delays it by d wavefronts, at most to the last. Levels of the first kernel are unchanged,
+ * and so is the depth. Paired kinds are left as they are. */
+void orc_place_g2(int32_t kind, int32_t n, int32_t *level, int32_t mode) {
+    if ((kind != 0 && kind != 3) || mode == 0) return;
+    int32_t depth = 0;
+    for (int64_t v = 0; v < 2LL * n; ++v)
+        if (level[v] + 1 > depth) depth = level[v] + 1;
+    for (int64_t v = n; v < 2LL * n; ++v) {
+        int64_t l = mode < 0 ? depth - 1 : (int64_t)level[v] + mode;
+        level[v] = (int32_t)(l < depth - 1 ? l : depth - 1);
+    }
+}
+
 int orc_order(int64_t nv, int32_t n, const int32_t *level, int32_t *order) {
     int32_t depth = 0;
     for (int64_t v = 0; v < nv; ++v)

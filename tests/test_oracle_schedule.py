@@ -266,3 +266,32 @@ def test_block_segments_are_independent_level_runs(kind, B):
         for i in range(n):
             for e in range(M.rowptr[i], M.rowptr[i + 1]):
                 assert seg_of[pos[i]] < seg_of[pos[n + int(M.colidx[e])]]
+
+
+@pytest.mark.parametrize("kind", [oracle.SEP, oracle.SEP_T])
+def test_g2_placement_keeps_every_edge_forward(kind):
+    # second-kernel vertices are sinks: placing them anywhere from their earliest wavefront to
+    # the last keeps the schedule valid (checked edge by edge by the validator), leaves the
+    # first kernel's levels and the depth alone, and moves later as the delay grows
+    w = I.spmv_trsv_powerlaw(n=700, k=1, mean=6, lmax=40, halfband=80, seed=23)
+    L, M = w.L, w.M
+    n = L.n_rows
+    what = oracle.COST_SEP if kind == oracle.SEP else oracle.COST_SEP_T
+    asap = oracle.levels(kind, L, M)
+    depth = int(asap.max()) + 1
+    prev = asap
+    for g2 in (1, 3, 17, 10 ** 6):
+        lev = oracle.levels(kind, L, M, g2)
+        assert np.array_equal(lev[:n], asap[:n])
+        assert np.all(lev[n:] >= prev[n:]) and np.all(lev[n:] <= depth - 1) and int(lev.max()) + 1 == depth
+        sch = oracle.schedule(kind, what, L, M, 30, g2=g2)
+        assert np.array_equal(sch["level"], lev)
+        assert oracle.validate(kind, L, M, sch["order"], sch["part_ptr"]) == 0
+        prev = lev
+    alap = oracle.levels(kind, L, M, -1)
+    assert np.all(alap[n:] == depth - 1) and np.array_equal(alap[:n], asap[:n])
+    assert np.array_equal(oracle.levels(kind, L, M, 10 ** 6), alap)
+    sch = oracle.schedule(kind, what, L, M, 30, g2=-1)
+    assert oracle.validate(kind, L, M, sch["order"], sch["part_ptr"]) == 0
+    # paired kinds ignore the placement
+    assert np.array_equal(oracle.levels(oracle.PAIRED, L, None, -1), oracle.levels(oracle.PAIRED, L, None))

@@ -83,7 +83,11 @@ typedef struct {
     int64_t part_cost_target; /* C of the partition cut (§3.1 vertex cost); 0 = auto  */
     int32_t lanes_per_row;    /* lanes of a warp working on one row: 1..32 (pow2); 0 = auto */
     int32_t rhs_tile;         /* right-hand-side columns handled side by side; 0 = auto */
-    int32_t g2_placement;     /* reserved, must be 0 (as-soon-as-possible placement) */
+    int32_t g2_placement;     /* separated schedules (SpTRSV -> SpMV forward, SpMV -> SpTRSV
+                                 adjoint): wavefront of the second kernel's vertices, which
+                                 are sinks of the joint DAG (slack, §3.2.2). 0: earliest;
+                                 -1: last wavefront; d > 0: delayed by d wavefronts (at most
+                                 to the last). Ignored by paired schedules. */
     int32_t blocks_per_sm;    /* resident executor blocks per SM; 0 = occupancy limit  */
     uint64_t timeout_ns;      /* limit of one dependence wait on the GPU; 0 = 2 s    */
     uint32_t flags;           /* SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE  */
@@ -211,6 +215,8 @@ typedef struct {
                                                      vertex is a first-kernel row (class 0; 0 for
                                                      paired schedules) */
     int32_t split_pct, adj_split_pct;             /* see sf_schedule_set_split */
+    int32_t g2_placement, adj_g2_placement;       /* see sf_options.g2_placement */
+    int32_t min_blocks, adj_min_blocks;           /* see sf_schedule_set_occupancy */
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -236,6 +242,12 @@ sf_status sf_schedule_set_launch(sf_schedule *sch, int32_t lanes_per_row, int32_
 sf_status sf_schedule_recut(sf_schedule *sch, int32_t which, int64_t part_cost_target,
                             int32_t lanes_per_row, int32_t team_lanes, void *stream);
 
+/* Re-places the second kernel's vertices of the forward (0), adjoint (1) or both (-1)
+ * separated schedules (g2_placement as in sf_options) and rebuilds their order, partition
+ * cut (same cost target) and row-block order; the earliest levels are kept from inspection.
+ * Paired schedules are left as they are. Synchronises `stream` before and after. */
+sf_status sf_schedule_replace(sf_schedule *sch, int32_t which, int32_t g2_placement, void *stream);
+
 /* Row-block executor (k = 1 with value flags, exec_mode 2): blocks of B consecutive rows
  * (in decreasing row order for the adjoint), each run by one CTA that keeps the block's
  * values in shared memory, so dependences inside a block never leave the SM; the CTA runs
@@ -255,6 +267,15 @@ sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_row
  * time the executor kernel alone with cudaEventElapsedTime. Both NULL stops the recording.
  * The events stay owned by the caller and must outlive the launches. No GPU work. */
 sf_status sf_schedule_set_exec_events(sf_schedule *sch, int32_t which, void *ev_start, void *ev_stop);
+
+/* Register budget of the partition executor's kernels for the forward (0), adjoint (1) or
+ * both (-1) schedules: min_blocks 1 (or 0, the default) lets the kernels keep all the
+ * registers they want, which suits schedules bound by their dependence chain; 3 selects
+ * variants compiled for three resident 256-thread blocks per SM (85 registers), which suits
+ * schedules bound by the number of rows in flight (many independent instances). The
+ * variants exist for value-flag launches (k = 1) with 1, 2 or 4 lanes per row and 32-lane
+ * teams; other launches use the default kernels. No GPU work. */
+sf_status sf_schedule_set_occupancy(sf_schedule *sch, int32_t which, int32_t min_blocks);
 
 /* Partition classes of the separated schedules (SpTRSV -> SpMV forward, SpMV -> SpTRSV
  * adjoint): with class0_pct in 1..99 that percent of the executor's teams run the partitions

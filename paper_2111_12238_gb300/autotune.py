@@ -3,8 +3,10 @@
 For one schedule and one way of running it, times candidate launch shapes on the GPU and
 keeps the fastest: for one right-hand side the row-block executor with several block sizes
 and lane counts, and the partition executor with several (lanes per row, team width, items
-per partition), then, for separated schedules, the best partition shape with the teams split
-between the two partition classes (``sf_schedule_set_split``). Candidates are applied without re-inspecting: ``sf_schedule_reblock``
+per partition), then, for separated schedules, the best shape with the second kernel's
+vertices placed later (``sf_schedule_replace``), the best partition shape on the executor's
+occupancy variants (``sf_schedule_set_occupancy``) and with the teams split between the two
+partition classes (``sf_schedule_set_split``). Candidates are applied without re-inspecting: ``sf_schedule_reblock``
 rebuilds the row-block order, ``sf_schedule_recut`` re-cuts the partitions for a new cost
 target (items per partition x mean vertex cost); levels are kept.
 Results are cached in a JSON file (``SF_TUNE_CACHE``, default
@@ -27,6 +29,7 @@ DEFAULT_TEAMS = (8, 32)
 DEFAULT_BLOCK_ROWS = (1024, 2048, 4096, 8192, 16384)
 DEFAULT_BLOCK_LANES = (1, 2, 4, 32)
 DEFAULT_SPLITS = (50, 65, 80, 90)
+DEFAULT_PLACEMENTS = (-1, 2, 8, 32)
 
 
 def _cache_path() -> str:
@@ -81,6 +84,8 @@ def _time(run: Callable[[], object], reps: int) -> float:
 
 def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     """Applies one candidate launch shape to direction `which` of the schedule."""
+    sched.replace(which, c.get("g2", 0))   # no-op unless the placement changes
+    sched.set_occupancy(which, c.get("occ", 1))
     if c["exec"] == "blocks":
         sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
         sched.set_split(which, 0)
@@ -95,7 +100,8 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
          k: int = 1, lanes: Sequence[int] = DEFAULT_LANES, items: Sequence[int] = DEFAULT_ITEMS,
          teams: Sequence[int] = DEFAULT_TEAMS, blocks: bool = True,
          block_rows: Sequence[int] = DEFAULT_BLOCK_ROWS, block_lanes: Sequence[int] = DEFAULT_BLOCK_LANES,
-         splits: Sequence[int] = DEFAULT_SPLITS, reps: int = 3, budget_s: float = 20.0,
+         splits: Sequence[int] = DEFAULT_SPLITS, placements: Sequence[int] = DEFAULT_PLACEMENTS, occupancy=True,
+         reps: int = 3, budget_s: float = 20.0,
          use_cache: bool = True) -> Dict:
     """Chooses the executor and its launch shape for `which` (0 forward, 1 adjoint) of
     `sched`, timing `run()` (one execution) for every candidate within `budget_s` seconds.
@@ -143,12 +149,37 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
         trials.append(dict(c, ms=ms))
         if best is None or ms < best["ms"]:
             best = trials[-1]
-    # separated schedules: the best partition shape with the teams split between the solve
-    # chain and the second-kernel rows
-    if best is not None and best["exec"] == "partitions" and splits and \
-            inf["parts_class0" if which == 0 else "adj_parts_class0"] > 0:
+    separated = inf["parts_class0" if which == 0 else "adj_parts_class0"] > 0
+    # separated schedules: the best shape with the second kernel's vertices placed later
+    # (slack, section 3.2.2), then with the teams split between the two partition classes
+    if best is not None and separated and placements:
+        for g2 in placements:
+            c = {kk: v for kk, v in best.items() if kk not in ("ms", "part_cost_target", "cached")}
+            c["g2"] = g2
+            try:
+                _apply(sched, which, c, mean)
+                ms = _time(run, reps)
+            except sf.SparseFusionError:
+                if c["exec"] != "blocks":
+                    raise
+                continue
+            sched.check()
+            trials.append(dict(c, ms=ms))
+            if ms < best["ms"]:
+                best = trials[-1]
+    # the best partition shape on the occupancy variants of the executor kernels
+    if best is not None and best["exec"] == "partitions" and k == 1 and occupancy and best.get("lanes", 32) <= 4:
+        c = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2")}
+        c["occ"] = 3
+        _apply(sched, which, c, mean)
+        ms = _time(run, reps)
+        sched.check()
+        trials.append(dict(c, ms=ms))
+        if ms < best["ms"]:
+            best = trials[-1]
+    if best is not None and best["exec"] == "partitions" and splits and separated:
         for pct in splits:
-            c = {k: v for k, v in best.items() if k in ("exec", "lanes", "items", "team")}
+            c = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "occ")}
             c["split"] = pct
             _apply(sched, which, c, mean)
             ms = _time(run, reps)

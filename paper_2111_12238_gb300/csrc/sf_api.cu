@@ -68,6 +68,9 @@ struct Dir {
     int *plist = nullptr;       // separated kinds: class-0 then class-1 partitions
     int n_parts0 = 0;           // class-0 partitions (first vertex in the first kernel)
     int split_pct = 0;          // percent of teams that run class 0 (0: one class for all)
+    int g2 = 0;                 // placement of second-kernel vertices (separated kinds)
+    int minb = 1;               // 1: register-rich executor kernels; 3: occupancy variants
+    int *level_asap = nullptr;  // separated kinds: the earliest (Kahn) levels, kept for re-placement
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // recorded around the executor kernel
     int *cost = nullptr;        // c(v) of every vertex (kept for re-cutting)
     long long cost_total = 0;
@@ -125,6 +128,7 @@ struct sf_schedule {
     int team = 0;               // 0: automatic (whole-warp teams)
     int block_rows = 0;         // rows per block of the row-block executor (0: automatic)
     int exec_mode = 0;          // 0 automatic, 1 partitions, 2 row blocks
+    int g2 = 0;                 // placement of second-kernel vertices at inspection
     bool epoch_flags = false;
     bool dynamic_queue = false;
     unsigned long long timeout_ns = 2000000000ull;
@@ -146,7 +150,6 @@ sf_status validate_options(const sf_options *o) {
         return fail(SF_ERR_INVALID_ARG, "lanes_per_row must be 0 or a power of two in [1, 32]");
     if (o->rhs_tile != 0 && !is_pow2_upto32(o->rhs_tile))
         return fail(SF_ERR_INVALID_ARG, "rhs_tile must be 0 or a power of two in [1, 32]");
-    if (o->g2_placement != 0) return fail(SF_ERR_INVALID_ARG, "g2_placement must be 0");
     if (o->team_lanes != 0 && o->team_lanes != 8 && o->team_lanes != 32)
         return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     if (o->block_rows < 0 || o->block_rows > (1 << 20))
@@ -296,6 +299,13 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     if (e == cudaErrorInvalidValue) return fail(SF_ERR_BAD_PATTERN, "inspector: the joint DAG has a cycle");
     if (e != cudaSuccess) return from_cuda(e, "Kahn peeling");
     if (timed_out) return fail(SF_ERR_TIMEOUT, "Kahn peeling: grid barrier timed out");
+    if (kind == K_SEP || kind == K_SEP_T) {
+        d.level_asap = (int *)S->keep.alloc(sizeof(int) * nv);
+        if (!d.level_asap) return fail(SF_ERR_OOM, "inspector: out of device memory");
+        SF_CK(cudaMemcpyAsync(d.level_asap, d.level, sizeof(int) * nv, cudaMemcpyDeviceToDevice, s), "inspector");
+        d.g2 = S->g2;
+        SF_CK(place_g2(n, d.depth, d.g2, d.level, s), "second-kernel placement");
+    }
     e = build_order(nv, n, d.level, d.depth, d.order, s, tmp);
     if (e != cudaSuccess) return from_cuda(e, "ordering");
     e = vertex_costs(what, n, S->L, S->hasM ? &S->M : nullptr, S->hasLT ? &S->LT : nullptr,
@@ -346,6 +356,7 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
     S->team = o.team_lanes;
     S->block_rows = o.block_rows;
     S->exec_mode = o.exec_mode;
+    S->g2 = o.g2_placement;
     int kind = K_PAIRED, what = 5;
     switch (S->pair) {
         case SF_TRSV_SPMV: kind = K_SEP; what = 0; break;
@@ -421,17 +432,18 @@ sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void 
     return SF_OK;
 }
 
-int occupancy(int mode, int dtype, int lpr, bool vf, int team) {
+int occupancy(int mode, int dtype, int lpr, bool vf, int team, int minb) {
     static std::mutex mu;
-    static int cache[M_COUNT][2][6][2][2] = {};
+    static int cache[M_COUNT][2][6][2][2][2] = {};
     int li = 0;
     while ((1 << li) < lpr) ++li;
     std::lock_guard<std::mutex> lk(mu);
-    int &c = cache[mode][dtype][li][vf ? 1 : 0][team == 8 ? 0 : 1];
+    int &c = cache[mode][dtype][li][vf ? 1 : 0][team == 8 ? 0 : 1][minb > 1 ? 1 : 0];
     if (!c) {
-        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf, team);
-        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV) c = occupancy_adj(mode, dtype, lpr, vf, team);
-        else c = occupancy_pair(mode, dtype, lpr, vf, team);
+        if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf, team, minb);
+        else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
+            c = occupancy_adj(mode, dtype, lpr, vf, team, minb);
+        else c = occupancy_pair(mode, dtype, lpr, vf, team, minb);
     }
     return c;
 }
@@ -508,7 +520,8 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         a.rdiag = d.aux;
         SF_CK(launch_rdiag(dtype, S->n, S->L.rowptr, a.Lv, vbuf, d.aux, d.st, s), "value-flag reset");
     }
-    int per_sm = occupancy(mode, dtype, lpr, vf, team);
+    const int minb = d.minb;
+    int per_sm = occupancy(mode, dtype, lpr, vf, team, minb);
     if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
     long long blocks = (long long)per_sm * S->sms;
     const long long teams_per_block = 8LL * (32 / team);
@@ -527,10 +540,10 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     }
     cudaError_t e;
     if (d.ev_start) SF_CK(cudaEventRecord(d.ev_start, s), "timing event");
-    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, team, (int)blocks, s, a);
+    if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, team, minb, (int)blocks, s, a);
     else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
-        e = launch_exec_adj(mode, dtype, lpr, vf, team, (int)blocks, s, a);
-    else e = launch_exec_pair(mode, dtype, lpr, vf, team, (int)blocks, s, a);
+        e = launch_exec_adj(mode, dtype, lpr, vf, team, minb, (int)blocks, s, a);
+    else e = launch_exec_pair(mode, dtype, lpr, vf, team, minb, (int)blocks, s, a);
     if (e != cudaSuccess) return from_cuda(e, "executor launch");
     if (d.ev_stop) SF_CK(cudaEventRecord(d.ev_stop, s), "timing event");
     return SF_OK;
@@ -870,6 +883,10 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     info->adj_parts_class0 = S->adj.n_parts0;
     info->split_pct = S->fwd.split_pct;
     info->adj_split_pct = S->adj.split_pct;
+    info->g2_placement = S->fwd.g2;
+    info->adj_g2_placement = S->adj.g2;
+    info->min_blocks = S->fwd.minb;
+    info->adj_min_blocks = S->adj.minb;
     info->block_segments = S->fwd.n_segs;
     info->adj_block_segments = S->adj.n_segs;
     info->block_threads = S->fwd.present ? block_threads(S->fwd) : 0;
@@ -947,6 +964,30 @@ SF_API sf_status sf_schedule_recut(sf_schedule *S, int32_t which, int64_t part_c
     return SF_OK;
 }
 
+SF_API sf_status sf_schedule_replace(sf_schedule *S, int32_t which, int32_t g2_placement, void *stream) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    cudaStream_t s = (cudaStream_t)stream;
+    SF_CK(cudaStreamSynchronize(s), "replace");
+    Arena tmp;
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w) {
+        Dir &d = *dirs[w];
+        if ((which != -1 && which != w) || !d.present || !d.level_asap || d.g2 == g2_placement) continue;
+        SF_CK(cudaMemcpyAsync(d.level, d.level_asap, sizeof(int) * d.nv, cudaMemcpyDeviceToDevice, s), "replace");
+        SF_CK(place_g2(S->n, d.depth, g2_placement, d.level, s), "second-kernel placement");
+        SF_CK(build_order(d.nv, S->n, d.level, d.depth, d.order, s, tmp), "ordering");
+        d.g2 = g2_placement;
+        sf_status st = cut_dir(S, d, d.C, s, tmp);
+        if (st != SF_OK) return st;
+        st = block_dir(S, d, d.B, s, tmp);
+        if (st != SF_OK) return st;
+    }
+    SF_CK(cudaStreamSynchronize(s), "replace");
+    return SF_OK;
+}
+
 SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t block_rows, int32_t exec_mode,
                                      int32_t lanes_per_row, void *stream) {
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
@@ -981,6 +1022,17 @@ SF_API sf_status sf_schedule_set_exec_events(sf_schedule *S, int32_t which, void
     if (!d.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
     d.ev_start = (cudaEvent_t)ev_start;
     d.ev_stop = (cudaEvent_t)ev_stop;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_occupancy(sf_schedule *S, int32_t which, int32_t min_blocks) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (min_blocks != 0 && min_blocks != 1 && min_blocks != 3) return fail(SF_ERR_INVALID_ARG, "min_blocks must be 0, 1 or 3");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w)
+        if ((which == -1 || which == w) && dirs[w]->present) dirs[w]->minb = min_blocks ? min_blocks : 1;
     return SF_OK;
 }
 

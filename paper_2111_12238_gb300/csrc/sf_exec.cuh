@@ -505,9 +505,12 @@ __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, un
 
 constexpr int kExecThreads = 256;
 
-#ifndef SF_MIN_BLOCKS
-#define SF_MIN_BLOCKS 1
-#endif
+// Resident blocks per SM the compiler budgets registers for: the default kernels keep all the
+// registers they want (latency-bound chains prefer fewer, faster threads); the occupancy
+// variants of value-flag kernels with up to four lanes per row are held to three blocks of
+// 256 threads (85 registers), for schedules bound by the number of rows in flight.
+constexpr int kMinBlocksDefault = 1;
+constexpr int kMinBlocksHigh = 3;
 
 // Next ticket of a team (its first lane draws it; the caller broadcasts it when needed, so
 // the atomic's latency overlaps the current partition's work).
@@ -519,8 +522,8 @@ __device__ __forceinline__ int draw_ticket(const ExecArgs &a, int tl) {
 // A warp is split into 32/TEAM teams of TEAM lanes; a team runs one partition at a time
 // with TEAM/LPR groups of LPR lanes (one item per group per round). Teams are the units of
 // the partition assignment, so small partitions do not leave lanes of a warp idle.
-template <int MODE, typename T, int LPR, bool VF, int TEAM>
-__global__ void __launch_bounds__(kExecThreads, SF_MIN_BLOCKS) k_exec(const ExecArgs a) {
+template <int MODE, typename T, int LPR, bool VF, int TEAM, int MINB>
+__global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
     static_assert(LPR <= TEAM && TEAM <= 32, "groups fit in a team");
     constexpr int G = TEAM / LPR;
     constexpr int NT = 32 / TEAM;
@@ -587,28 +590,43 @@ __global__ void __launch_bounds__(kExecThreads, SF_MIN_BLOCKS) k_exec(const Exec
 }
 
 template <int MODE, bool VF, int TEAM>
-const void *kernel_for_team(int dtype, int lpr) {
+const void *kernel_for_team(int dtype, int lpr, int minb) {
+    constexpr int D = kMinBlocksDefault;
+    if constexpr (VF && TEAM == 32) {
+        if (minb >= kMinBlocksHigh) {
+            constexpr int H = kMinBlocksHigh;
+            if (dtype == 0) {
+                if (lpr == 1) return (const void *)k_exec<MODE, double, 1, VF, 32, H>;
+                if (lpr == 2) return (const void *)k_exec<MODE, double, 2, VF, 32, H>;
+                if (lpr == 4) return (const void *)k_exec<MODE, double, 4, VF, 32, H>;
+            } else {
+                if (lpr == 1) return (const void *)k_exec<MODE, float, 1, VF, 32, H>;
+                if (lpr == 2) return (const void *)k_exec<MODE, float, 2, VF, 32, H>;
+                if (lpr == 4) return (const void *)k_exec<MODE, float, 4, VF, 32, H>;
+            }
+        }
+    }
     if (dtype == 0) {
         switch (lpr) {
-            case 1: return (const void *)k_exec<MODE, double, 1, VF, TEAM>;
-            case 2: return (const void *)k_exec<MODE, double, 2, VF, TEAM>;
-            case 4: return (const void *)k_exec<MODE, double, 4, VF, TEAM>;
-            case 8: return (const void *)k_exec<MODE, double, 8, VF, TEAM>;
+            case 1: return (const void *)k_exec<MODE, double, 1, VF, TEAM, D>;
+            case 2: return (const void *)k_exec<MODE, double, 2, VF, TEAM, D>;
+            case 4: return (const void *)k_exec<MODE, double, 4, VF, TEAM, D>;
+            case 8: return (const void *)k_exec<MODE, double, 8, VF, TEAM, D>;
         }
         if constexpr (TEAM == 32) {
-            if (lpr == 16) return (const void *)k_exec<MODE, double, 16, VF, 32>;
-            if (lpr == 32) return (const void *)k_exec<MODE, double, 32, VF, 32>;
+            if (lpr == 16) return (const void *)k_exec<MODE, double, 16, VF, 32, D>;
+            if (lpr == 32) return (const void *)k_exec<MODE, double, 32, VF, 32, D>;
         }
     } else {
         switch (lpr) {
-            case 1: return (const void *)k_exec<MODE, float, 1, VF, TEAM>;
-            case 2: return (const void *)k_exec<MODE, float, 2, VF, TEAM>;
-            case 4: return (const void *)k_exec<MODE, float, 4, VF, TEAM>;
-            case 8: return (const void *)k_exec<MODE, float, 8, VF, TEAM>;
+            case 1: return (const void *)k_exec<MODE, float, 1, VF, TEAM, D>;
+            case 2: return (const void *)k_exec<MODE, float, 2, VF, TEAM, D>;
+            case 4: return (const void *)k_exec<MODE, float, 4, VF, TEAM, D>;
+            case 8: return (const void *)k_exec<MODE, float, 8, VF, TEAM, D>;
         }
         if constexpr (TEAM == 32) {
-            if (lpr == 16) return (const void *)k_exec<MODE, float, 16, VF, 32>;
-            if (lpr == 32) return (const void *)k_exec<MODE, float, 32, VF, 32>;
+            if (lpr == 16) return (const void *)k_exec<MODE, float, 16, VF, 32, D>;
+            if (lpr == 32) return (const void *)k_exec<MODE, float, 32, VF, 32, D>;
         }
     }
     return nullptr;
@@ -616,23 +634,24 @@ const void *kernel_for_team(int dtype, int lpr) {
 
 // Teams of 8 lanes serve lanes-per-row up to 8; wider rows use whole-warp teams.
 template <int MODE, bool VF>
-const void *kernel_for(int dtype, int lpr, int team) {
-    if (team == 8 && lpr <= 8) return kernel_for_team<MODE, VF, 8>(dtype, lpr);
-    return kernel_for_team<MODE, VF, 32>(dtype, lpr);
+const void *kernel_for(int dtype, int lpr, int team, int minb) {
+    if (team == 8 && lpr <= 8) return kernel_for_team<MODE, VF, 8>(dtype, lpr, minb);
+    return kernel_for_team<MODE, VF, 32>(dtype, lpr, minb);
 }
 
 template <int MODE>
-const void *kernel_for_mode(int dtype, int lpr, bool vf, int team) {
+const void *kernel_for_mode(int dtype, int lpr, bool vf, int team, int minb) {
     if constexpr (mode_has_vf(MODE)) {
-        if (vf) return kernel_for<MODE, true>(dtype, lpr, team);
+        if (vf) return kernel_for<MODE, true>(dtype, lpr, team, minb);
     }
-    return kernel_for<MODE, false>(dtype, lpr, team);
+    return kernel_for<MODE, false>(dtype, lpr, team, minb);
 }
 
-// Launches k_exec for a runtime (dtype, lanes-per-row, value flags, team lanes).
+// Launches k_exec for a runtime (dtype, lanes-per-row, value flags, team lanes, occupancy).
 template <int MODE>
-cudaError_t launch_mode(int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s, const ExecArgs &a) {
-    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf, team);
+cudaError_t launch_mode(int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
+                        const ExecArgs &a) {
+    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf, team, minb);
     if (!f) return cudaErrorInvalidValue;
     void *args[] = {(void *)&a};
     if (a.dynamic) return cudaLaunchKernel(f, dim3(blocks), dim3(kExecThreads), args, 0, s);
@@ -640,9 +659,9 @@ cudaError_t launch_mode(int dtype, int lpr, bool vf, int team, int blocks, cudaS
 }
 
 template <int MODE>
-int blocks_per_sm_mode(int dtype, int lpr, bool vf, int team) {
+int blocks_per_sm_mode(int dtype, int lpr, bool vf, int team, int minb) {
     int nb = 0;
-    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf, team);
+    const void *f = kernel_for_mode<MODE>(dtype, lpr, vf, team, minb);
     if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kExecThreads, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }

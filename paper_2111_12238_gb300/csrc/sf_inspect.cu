@@ -612,6 +612,23 @@ cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs
     return cudaStreamSynchronize(s);
 }
 
+// Placement of the second kernel's vertices of a separated schedule by their slack (§3.2.2):
+// they are sinks of the joint DAG, so mode < 0 moves them to the last wavefront, mode d > 0
+// delays them by d wavefronts (at most to the last); the first kernel's levels stay.
+__global__ void k_place_g2(int n, int depth, int mode, int *__restrict__ level) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int *l = level + n + t;
+        const long long v = mode < 0 ? (long long)depth - 1 : (long long)*l + mode;
+        *l = (int)(v < depth - 1 ? v : depth - 1);
+    }
+}
+
+cudaError_t place_g2(int n, int depth, int mode, int *level, cudaStream_t s) {
+    if (mode == 0) return cudaSuccess;
+    k_place_g2<<<grid_for(n, 256, 4096), 256, 0, s>>>(n, depth, mode, level);
+    return cudaGetLastError();
+}
+
 // Partition classes of a separated schedule: class 1 when the partition's first vertex is a
 // second-kernel row (a sink of the joint DAG), else class 0. plist lists the class-0
 // partitions in increasing order, then the class-1 partitions in increasing order.

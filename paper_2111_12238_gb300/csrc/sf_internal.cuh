@@ -79,11 +79,11 @@ struct ExecArgs {
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
 // Static assignment needs every block resident: those launches are cooperative.
-cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
+cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                             const ExecArgs &a);
-cudaError_t launch_exec_pair(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
+cudaError_t launch_exec_pair(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                             const ExecArgs &a);
-cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int team, int blocks, cudaStream_t s,
+cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                             const ExecArgs &a);
 // Row-block executor (k = 1): launch and blocks per SM for B rows of shared values and
 // `threads` threads per CTA (a multiple of 32, at most kBlockMaxThreads).
@@ -96,9 +96,9 @@ size_t block_exec_smem(int mode, int dtype, int block_rows);
 // and writes rdiag[i] = 1 / L_ii (L's diagonal is the last entry of each row).
 cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void *vec, void *rdiag, ExecState *st,
                          cudaStream_t s);
-int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team);
-int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team);
-int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team);
+int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb);
+int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team, int minb);
+int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team, int minb);
 // Adjoint helpers: dst[t] = src[perm[t]] (values in transposed order), and the value
 // gradients out[e] = sign * sum_c coef[i*k+c] * vec[col(e)*k+c] over the rows i of a pattern.
 cudaError_t launch_gather_vals(int dtype, long long nnz, const int *perm, const void *src, void *dst, cudaStream_t s);

@@ -58,7 +58,9 @@ class SfInfo(C.Structure):
                 ("block_segments", C.c_int32), ("adj_block_segments", C.c_int32),
                 ("block_threads", C.c_int32), ("adj_block_threads", C.c_int32),
                 ("parts_class0", C.c_int32), ("adj_parts_class0", C.c_int32),
-                ("split_pct", C.c_int32), ("adj_split_pct", C.c_int32)]
+                ("split_pct", C.c_int32), ("adj_split_pct", C.c_int32),
+                ("g2_placement", C.c_int32), ("adj_g2_placement", C.c_int32),
+                ("min_blocks", C.c_int32), ("adj_min_blocks", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -90,6 +92,8 @@ _SIGS = {
     "sf_schedule_reblock": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
     "sf_schedule_export_blocks": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "sf_schedule_set_split": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_replace": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
+    "sf_schedule_set_occupancy": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_set_exec_events": (C.c_int, [_P, C.c_int32, _P, _P]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
@@ -189,8 +193,10 @@ class DeviceCsr:
 
 
 def _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm=0,
-             epoch_flags=False, dynamic_queue=False, team_lanes=0, block_rows=0, exec_mode=0) -> SfOptions:
+             epoch_flags=False, dynamic_queue=False, team_lanes=0, block_rows=0, exec_mode=0,
+             g2_placement=0) -> SfOptions:
     o = SfOptions()
+    o.g2_placement = int(g2_placement)
     o.part_cost_target = int(part_cost_target)
     o.lanes_per_row = int(lanes_per_row)
     o.rhs_tile = int(rhs_tile)
@@ -304,6 +310,18 @@ class Schedule:
         _check(load_library().sf_schedule_set_exec_events(self.handle, int(which), hs or None, he or None),
                "sf_schedule_set_exec_events")
 
+    def replace(self, which=-1, g2_placement=0, stream=None):
+        """Re-places the second kernel's vertices of a separated schedule (0 earliest
+        wavefront, -1 last, d > 0 delayed by d) and rebuilds order, cut and row blocks."""
+        _check(load_library().sf_schedule_replace(self.handle, int(which), int(g2_placement), _stream(stream)),
+               "sf_schedule_replace")
+
+    def set_occupancy(self, which=-1, min_blocks=0):
+        """Executor kernels budgeted for min_blocks resident blocks per SM (1 default, 3 for
+        schedules bound by rows in flight)."""
+        _check(load_library().sf_schedule_set_occupancy(self.handle, int(which), int(min_blocks)),
+               "sf_schedule_set_occupancy")
+
     def set_split(self, which=-1, class0_pct=0):
         """Runs the partitions that open with a first-kernel row on class0_pct percent of the
         teams (separated schedules; 0 = one class)."""
@@ -347,10 +365,11 @@ class Schedule:
 
 def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjoint=False, part_cost_target=0,
             lanes_per_row=0, rhs_tile=0, timeout_ns=0, blocks_per_sm=0, epoch_flags=False,
-            dynamic_queue=False, team_lanes=0, block_rows=0, exec_mode=0, stream=None) -> Schedule:
+            dynamic_queue=False, team_lanes=0, block_rows=0, exec_mode=0, g2_placement=0,
+            stream=None) -> Schedule:
     lib = load_library()
     o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
-                 dynamic_queue, team_lanes, block_rows, exec_mode)
+                 dynamic_queue, team_lanes, block_rows, exec_mode, g2_placement)
     Ls = L.struct()
     Ms = M.struct() if M is not None else None
     h = C.c_void_p()
@@ -363,10 +382,10 @@ def inspect(pair: str, L: DeviceCsr, M: Optional[DeviceCsr] = None, *, want_adjo
 def inspect_batched(pair: str, Ls: Sequence[DeviceCsr], Ms: Optional[Sequence[DeviceCsr]] = None, *,
                     want_adjoint=False, part_cost_target=0, lanes_per_row=0, rhs_tile=0, timeout_ns=0,
                     blocks_per_sm=0, epoch_flags=False, dynamic_queue=False, team_lanes=0, block_rows=0,
-                    exec_mode=0, stream=None) -> Schedule:
+                    exec_mode=0, g2_placement=0, stream=None) -> Schedule:
     lib = load_library()
     o = _options(want_adjoint, part_cost_target, lanes_per_row, rhs_tile, timeout_ns, blocks_per_sm, epoch_flags,
-                 dynamic_queue, team_lanes, block_rows, exec_mode)
+                 dynamic_queue, team_lanes, block_rows, exec_mode, g2_placement)
     cnt = len(Ls)
     la = (SfCsr * cnt)(*[x.struct() for x in Ls])
     ma = (SfCsr * cnt)(*[x.struct() for x in Ms]) if Ms is not None else None

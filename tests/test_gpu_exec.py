@@ -312,3 +312,60 @@ def test_partition_class_split_is_exact(pct):
     gb = s2.adjoint(Lv2, Av, t(p.gy), saved=z, x_in=xin, gx=gx)
     s2.check()
     assert col_rel_err(host(gb), gb_ref) < 1e-12 and col_rel_err(host(gx), gx_ref) < 1e-12
+
+
+@pytest.mark.parametrize("g2", [-1, 2, 40])
+def test_g2_placement_is_exact(g2):
+    # forward SpTRSV -> SpMV and the SpMV -> SpTRSV adjoint with second-kernel rows placed late
+    need_cuda()
+    w = _lap3d(12, 1)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), g2_placement=g2)
+    Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
+    xs = torch.empty_like(b)
+    y = sch.execute(Lv, Mv, b=b, x_save=xs)
+    sch.check()
+    assert col_rel_err(host(xs), x_ref) < 1e-12 and col_rel_err(host(y), y_ref) < 1e-12
+    for mode in (1, 2):
+        sch.reblock(0, 2048, mode, 0)
+        y = sch.execute(Lv, Mv, b=b, x_save=xs)
+        sch.check()
+        assert col_rel_err(host(y), y_ref) < 1e-12
+    p = I.spmv_trsv_powerlaw(n=6000, k=1, mean=10, lmax=80, halfband=400, seed=41)
+    z_ref = oracle.spmv_trsv(p.M, p.L, p.x_in, p.b)
+    gb_ref, gx_ref, _, _ = oracle.adj_spmv_trsv(p.M, p.L, p.x_in, z_ref, p.gy)
+    s2 = sf.inspect("spmv_trsv", dev_csr(p.L), dev_csr(p.M), want_adjoint=True)
+    s2.replace(1, g2)
+    Lv2, Av, xin = t(p.L.vals), t(p.M.vals), t(p.x_in)
+    z = s2.execute(Lv2, Av, b=t(p.b), x_in=xin)
+    gx = torch.empty_like(xin)
+    gb = s2.adjoint(Lv2, Av, t(p.gy), saved=z, x_in=xin, gx=gx)
+    s2.check()
+    assert col_rel_err(host(gb), gb_ref) < 1e-12 and col_rel_err(host(gx), gx_ref) < 1e-12
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_occupancy_variants_are_exact(lanes):
+    # kernels budgeted for three resident blocks per SM (lanes above 4 fall back to the
+    # default kernels): forward, adjoint and the SpTRSV-alone path
+    need_cuda()
+    w = _lap3d(12, 1)
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    gb_ref, gL_ref, gM_ref = oracle.adj_trsv_spmv(w.L, w.M, x_ref, w.gy)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, lanes_per_row=lanes)
+    sch.set_occupancy(-1, 3)
+    inf = sch.info()
+    assert inf["min_blocks"] == 3 and inf["adj_min_blocks"] == 3
+    Lv, Mv, b, gy = t(w.L.vals), t(w.M.vals), t(w.b), t(w.gy)
+    xs = torch.empty_like(b)
+    y = sch.execute(Lv, Mv, b=b, x_save=xs)
+    gL, gM = torch.empty_like(Lv), torch.empty_like(Mv)
+    gb = sch.adjoint(Lv, Mv, gy, saved=xs, gL=gL, gM=gM)
+    sch.check()
+    assert col_rel_err(host(y), y_ref) < 1e-12 and col_rel_err(host(gb), gb_ref) < 1e-12
+    assert vec_rel_err(host(gL), gL_ref) < 1e-12 and vec_rel_err(host(gM), gM_ref) < 1e-12
+    s2 = sf.inspect("trsv", dev_csr(w.L), lanes_per_row=lanes)
+    s2.set_occupancy(0, 3)
+    x = s2.execute(Lv, b=b)
+    s2.check()
+    assert col_rel_err(host(x), x_ref) < 1e-12

@@ -122,3 +122,29 @@ def test_invalid_patterns_rejected():
     with pytest.raises(sf.SparseFusionError) as e:
         sf.inspect("ic0_trsv", dev_csr(L), want_adjoint=True)
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("g2", [-1, 1, 6])
+def test_g2_placement_matches_oracle(g2):
+    # second-kernel vertices placed by slack, at inspection and by re-placement afterwards
+    need_cuda()
+    w = _workloads()["lap3d13_ragged"]()
+    p = _workloads()["powerlaw"]()
+    for pair, ww, kinds in (("trsv_spmv", w, [KIND_OF["trsv_spmv"]]),
+                            ("spmv_trsv", p, [KIND_OF["spmv_trsv"], ADJ_OF["spmv_trsv"]])):
+        for via_replace in (False, True):
+            sch = sf.inspect(pair, dev_csr(ww.L), dev_csr(ww.M), want_adjoint=pair == "spmv_trsv",
+                             part_cost_target=57, g2_placement=0 if via_replace else g2)
+            if via_replace:
+                sch.replace(-1, g2)
+            sch.validate()
+            info = sch.info()
+            for which, (kind, what) in enumerate(kinds):
+                sep = kind in (oracle.SEP, oracle.SEP_T)
+                ref = oracle.schedule(kind, what, ww.L, ww.M, 57, wide=info["wide_cost" if which == 0 else "adj_wide_cost"],
+                                      g2=g2 if sep else 0)
+                got = sch.export(which)
+                assert np.array_equal(got["level"], ref["level"])
+                assert np.array_equal(got["order"], ref["order"])
+                assert np.array_equal(got["part_ptr"], ref["part_ptr"])
+                assert info["g2_placement" if which == 0 else "adj_g2_placement"] == (g2 if sep else 0)

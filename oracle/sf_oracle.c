@@ -330,9 +330,6 @@ int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, c
     return OK;
 }
 
-/* Linearised order of the joint DAG: vertices sorted by (level, tag, row), the canonical
- * tie-break among the many valid topological orders. Vertex v = tag*n + row is encoded as
- * row | tag << 31. Counting sort by level over vertices in increasing v. */
 /* Placement of the second kernel's vertices in a separated schedule (kinds 0 and 3), using
  * their slack (§3.2.2): such a vertex (an SpMV row, or an A^T row of the adjoint) is a sink of
  * the joint DAG, so any wavefront from its earliest one (the longest-path level) to the last
@@ -351,6 +348,9 @@ void orc_place_g2(int32_t kind, int32_t n, int32_t *level, int32_t mode) {
     }
 }
 
+/* Linearised order of the joint DAG: vertices sorted by (level, tag, row), the canonical
+ * tie-break among the many valid topological orders. Vertex v = tag*n + row is encoded as
+ * row | tag << 31. Counting sort by level over vertices in increasing v. */
 int orc_order(int64_t nv, int32_t n, const int32_t *level, int32_t *order) {
     int32_t depth = 0;
     for (int64_t v = 0; v < nv; ++v)

@@ -154,7 +154,7 @@ sf_status validate_options(const sf_options *o) {
         return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     if (o->block_rows < 0 || o->block_rows > (1 << 20))
         return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
-    if (o->exec_mode < 0 || o->exec_mode > 2) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0, 1 or 2");
+    if (o->exec_mode < 0 || o->exec_mode > 3) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0, 1, 2 or 3");
     if (o->blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
     if (o->flags & ~(SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE))
         return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
@@ -490,6 +490,28 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     const int dtype = dt == SF_F64 ? 0 : 1;
     void *vbuf = value_flag_buffer(mode, a);
     const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
+    // warp-specialised row-block executor
+    if (vf && d.exec_mode == 3 && d.nb > 0) {
+        // consumer threads: one per position of the widest segment, a power of two in [32, 256]
+        const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
+        const int rows = std::min(d.B, S->n);
+        const int occ = block_ws_fits(mode, dtype, rows, nc);
+        if (occ <= 0) return fail(SF_ERR_UNSUPPORTED, "row blocks of %d rows do not fit in shared memory", d.B);
+        a.aux = d.aux;
+        a.order = d.border;
+        a.bdesc = d.bdesc;
+        a.block_ptr = d.block_ptr;
+        a.seg_ptr = d.seg_ptr;
+        a.block_seg = d.block_seg;
+        a.block_rows = d.B;
+        a.n_blocks = d.nb;
+        a.block_rev = (d.kind == K_PAIRED_T || d.kind == K_SEP_T) ? 1 : 0;
+        long long blocks = std::min<long long>((long long)occ * S->sms, d.nb);
+        blocks = std::max<long long>(blocks, 1);
+        cudaError_t e = launch_block_ws(mode, dtype, (int)blocks, nc, s, a, d.ev_start, d.ev_stop);
+        if (e != cudaSuccess) return from_cuda(e, "row-block executor launch");
+        return SF_OK;
+    }
     // the row-block executor serves one right-hand side with value flags (its pre-pass
     // resets the published vector)
     if (vf && d.exec_mode == 2 && d.nb > 0) {
@@ -993,7 +1015,7 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
     if (block_rows < 0 || block_rows > (1 << 20)) return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
-    if (exec_mode < -1 || exec_mode > 2) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1, 0, 1 or 2");
+    if (exec_mode < -1 || exec_mode > 3) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1, 0, 1, 2 or 3");
     if (lanes_per_row != 0 && lanes_per_row != 1 && lanes_per_row != 2 && lanes_per_row != 4 && lanes_per_row != 32)
         return fail(SF_ERR_INVALID_ARG, "row-block lanes per row must be 1, 2, 4 or 32");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "sf_block.cuh"
+#include "sf_block_ws.cuh"
 
 namespace sf {
 
@@ -13,6 +14,19 @@ const void *block_kernel_lpr(int lpr) {
         case 2: return (const void *)k_block_exec<MODE, T, 2>;
         case 4: return (const void *)k_block_exec<MODE, T, 4>;
         case 32: return (const void *)k_block_exec<MODE, T, 32>;
+        default: return nullptr;
+    }
+}
+
+// Warp-specialised row-block kernel of a mode.
+template <typename T>
+const void *block_ws_kernel_t(int mode) {
+    switch (mode) {
+        case M_TRSV_SPMV: return (const void *)k_block_ws<M_TRSV_SPMV, T>;
+        case M_TRSV: return (const void *)k_block_ws<M_TRSV, T>;
+        case M_SPMV_TRSV: return (const void *)k_block_ws<M_SPMV_TRSV, T>;
+        case M_ADJ_TRSV_SPMV: return (const void *)k_block_ws<M_ADJ_TRSV_SPMV, T>;
+        case M_ADJ_SPMV_TRSV: return (const void *)k_block_ws<M_ADJ_SPMV_TRSV, T>;
         default: return nullptr;
     }
 }
@@ -34,5 +48,7 @@ const void *block_kernel_t(int mode, int lpr) {
 
 const void *block_kernel_f64(int mode, int lpr);
 const void *block_kernel_f32(int mode, int lpr);
+const void *block_ws_kernel_f64(int mode);
+const void *block_ws_kernel_f32(int mode);
 
 }  // namespace sf

@@ -7,6 +7,7 @@
 namespace sf {
 
 const void *block_kernel_f64(int mode, int lpr) { return block_kernel_t<double>(mode, lpr); }
+const void *block_ws_kernel_f64(int mode) { return block_ws_kernel_t<double>(mode); }
 
 namespace {
 
@@ -57,6 +58,46 @@ int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threa
         return 0;
     }
     return nb;
+}
+
+size_t block_ws_smem(int dtype, int rows, int nc) {
+    const size_t es = dtype == 0 ? 8 : 4;
+    const size_t stage = dtype == 0 ? ws_stage_bytes<double>(nc) : ws_stage_bytes<float>(nc);
+    return (((size_t)rows * es + 15) & ~(size_t)15) + (size_t)kWsStages * stage + ws_desc_bytes(nc);
+}
+
+int block_ws_fits(int mode, int dtype, int rows, int nc) {
+    const void *f = dtype == 0 ? block_ws_kernel_f64(mode) : block_ws_kernel_f32(mode);
+    if (!f || nc < 32 || nc > kWsMaxConsumers || (nc & (nc - 1))) return 0;
+    const size_t smem = block_ws_smem(dtype, rows, nc);
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, nc + kWsProducers, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_block_ws(int mode, int dtype, int blocks, int nc, cudaStream_t s, const ExecArgs &a,
+                            cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+    const void *prep = block_kernel(mode, dtype, 0);
+    const void *f = dtype == 0 ? block_ws_kernel_f64(mode) : block_ws_kernel_f32(mode);
+    if (!prep || !f || nc < 32 || nc > kWsMaxConsumers || (nc & (nc - 1))) return cudaErrorInvalidValue;
+    void *args[] = {(void *)&a};
+    const long long pb = std::min<long long>(((long long)a.n + 255) / 256, 65535LL);
+    cudaError_t e = cudaLaunchKernel(prep, dim3((unsigned)std::max<long long>(pb, 1)), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = block_ws_smem(dtype, std::min(a.block_rows, a.n), nc);
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ev_start && (e = cudaEventRecord(ev_start, s)) != cudaSuccess) return e;
+    e = cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(nc + kWsProducers), args, smem, s);
+    if (e != cudaSuccess) return e;
+    return ev_stop ? cudaEventRecord(ev_stop, s) : cudaSuccess;
 }
 
 cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int threads, cudaStream_t s,

@@ -3,4 +3,5 @@
 
 namespace sf {
 const void *block_kernel_f32(int mode, int lpr) { return block_kernel_t<float>(mode, lpr); }
+const void *block_ws_kernel_f32(int mode) { return block_ws_kernel_t<float>(mode); }
 }  // namespace sf

@@ -92,6 +92,11 @@ cudaError_t launch_block_exec(int mode, int dtype, int lpr, int blocks, int thre
                               const ExecArgs &a, cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 int block_exec_occupancy(int mode, int dtype, int lpr, int block_rows, int threads);
 size_t block_exec_smem(int mode, int dtype, int block_rows);
+// Warp-specialised row-block executor: nc consumer threads (32, 64, 128 or 256) plus
+// 512 producer threads; resident CTAs per SM (0: does not fit) and launch.
+int block_ws_fits(int mode, int dtype, int rows, int nc);
+cudaError_t launch_block_ws(int mode, int dtype, int blocks, int nc, cudaStream_t s, const ExecArgs &a,
+                            cudaEvent_t ev_start, cudaEvent_t ev_stop);
 // Pre-pass of partition launches with value flags: resets vec[0..n) to the all-ones pattern
 // and writes rdiag[i] = 1 / L_ii (L's diagonal is the last entry of each row).
 cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void *vec, void *rdiag, ExecState *st,

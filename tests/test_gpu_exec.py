@@ -246,6 +246,8 @@ def test_recut_and_autotune_keep_results_exact():
         if r["exec"] == "blocks":
             assert inf[pre + "exec_mode"] == 2 and inf[pre + "block_lanes"] == r["block_lanes"]
             assert inf[pre + "block_rows"] == r["block_rows"]
+        elif r["exec"] == "ws":
+            assert inf[pre + "exec_mode"] == 3 and inf[pre + "block_rows"] == r["block_rows"]
         else:
             assert inf[pre + "exec_mode"] == 1 and r["lanes"] in autotune.DEFAULT_LANES
             assert inf[pre + "lanes_per_row"] == r["lanes"]
@@ -255,9 +257,11 @@ def test_recut_and_autotune_keep_results_exact():
     sch.validate()
     assert col_rel_err(host(y), y_ref) < 1e-12
     assert col_rel_err(host(gb), gb_ref) < 1e-12
-    # the re-cut schedule equals the oracle's cut for the same target and wide threshold
+    # the re-cut schedule equals the oracle's cut for the same target, wide threshold and
+    # placement of the second kernel's rows
     got = sch.export(0)
-    ref = oracle.schedule(oracle.SEP, oracle.COST_SEP, w.L, w.M, inf["part_cost_target"], wide=inf["wide_cost"])
+    ref = oracle.schedule(oracle.SEP, oracle.COST_SEP, w.L, w.M, inf["part_cost_target"], wide=inf["wide_cost"],
+                          g2=inf["g2_placement"])
     assert np.array_equal(got["part_ptr"], ref["part_ptr"])
     assert p0 > 0
 

@@ -95,9 +95,10 @@ typedef struct {
                                  (several teams per warp); 0 = 32 */
     int32_t block_rows;       /* rows per block of the row-block executor; 0 = min(8192, n) */
     int32_t exec_mode;        /* 0 (automatic) and 1: partitions; 2: row blocks; 3: row blocks
-                                 with warp-specialised loading (2 and 3: k = 1 with value
-                                 flags; the call fails when a block does not fit in shared
-                                 memory). The autotuner chooses between them. */
+                                 with warp-specialised loading (cp.async); 4: row blocks with
+                                 packed records and bulk copies (2-4: k = 1 with value flags;
+                                 the call fails when a block does not fit in shared memory).
+                                 The autotuner chooses between them. */
 } sf_options;
 
 /* Opaque fused schedule (§3.1 "fused partitioning", the FusedSchedule of Figure 3b).
@@ -257,8 +258,9 @@ sf_status sf_schedule_replace(sf_schedule *sch, int32_t which, int32_t g2_placem
  * (one rounding more than a division). Rebuilds the block
  * order of the forward (0), adjoint (1) or both (-1) schedules for block_rows rows
  * (0 keeps the current size), sets exec_mode (-1 keeps; 0 automatic, 1 partitions,
- * 2 row blocks, 3 warp-specialised row blocks) and the row-block lanes per row (1, 2, 4 or
- * 32; 0 keeps; exec_mode 3 runs one consumer thread per row). Synchronises
+ * 2 row blocks, 3 warp-specialised row blocks, 4 row blocks with packed records, built
+ * here) and the row-block lanes per row (1, 2, 4 or 32; 0 keeps; exec_modes 3 and 4 run one
+ * consumer thread per row). Synchronises
  * `stream` before and after. */
 sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,
                               int32_t lanes_per_row, void *stream);

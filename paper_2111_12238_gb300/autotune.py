@@ -1,8 +1,9 @@
 """Autotuner of the executor's launch shape.
 
 For one schedule and one way of running it, times candidate launch shapes on the GPU and
-keeps the fastest: for one right-hand side the warp-specialised and the plain row-block
-executors with several block sizes (and lane counts), and the partition executor with several (lanes per row, team width, items
+keeps the fastest: for one right-hand side the row-block executors (warp-specialised with
+cp.async or with packed records and bulk copies, and the plain one) with several block sizes
+(and lane counts), and the partition executor with several (lanes per row, team width, items
 per partition), then, for separated schedules, the best shape with the second kernel's
 vertices placed later (``sf_schedule_replace``), the best partition shape on the executor's
 occupancy variants (``sf_schedule_set_occupancy``) and with the teams split between the two
@@ -89,8 +90,8 @@ def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     if c["exec"] == "blocks":
         sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
         sched.set_split(which, 0)
-    elif c["exec"] == "ws":
-        sched.reblock(which, c["block_rows"], 3, 0)
+    elif c["exec"] in ("ws", "tma"):
+        sched.reblock(which, c["block_rows"], 3 if c["exec"] == "ws" else 4, 0)
         sched.set_split(which, 0)
     else:
         c["part_cost_target"] = max(1, c["items"] * mean)
@@ -124,19 +125,17 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
         best = cache[key]
         _apply(sched, which, best, mean)
         return dict(best, cached=True)
-    cands = []
-    if k == 1 and blocks:
-        n = inf["n"]
-        for B in block_rows:
-            if B <= 2 * max(n, 1):
-                cands.append({"exec": "ws", "block_rows": B})
-        for B in block_rows:
-            if B <= 2 * max(n, 1):
-                for L in block_lanes:
-                    cands.append({"exec": "blocks", "block_rows": B, "block_lanes": L})
+    # partition shapes first (the default executor; they finish the budget with a sound
+    # choice), then the row-block executors
     pc = [(L, p, T) for L in lanes if L >= kt for T in teams if T >= L for p in items if p <= max(1, T // L) * 4]
     pc.sort(key=lambda c: (abs(c[0] - max(1, kt)), c[2] != 32, abs(c[1] - 8)))
-    cands += [{"exec": "partitions", "lanes": L, "items": p, "team": T} for L, p, T in pc]
+    cands = [{"exec": "partitions", "lanes": L, "items": p, "team": T} for L, p, T in pc]
+    if k == 1 and blocks:
+        n = inf["n"]
+        sizes = [B for B in block_rows if B <= 2 * max(n, 1)]
+        cands += [{"exec": "ws", "block_rows": B} for B in sizes]
+        cands += [{"exec": "tma", "block_rows": B} for B in sizes]
+        cands += [{"exec": "blocks", "block_rows": B, "block_lanes": L} for B in sizes for L in block_lanes]
     t0 = time.perf_counter()
     trials = []
     best = None
@@ -148,7 +147,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
             ms = _time(run, reps)
         except sf.SparseFusionError:
             # a row-block size whose shared-memory footprint does not fit this direction
-            if c["exec"] not in ("blocks", "ws"):
+            if c["exec"] not in ("blocks", "ws", "tma"):
                 raise
             continue
         sched.check()
@@ -166,7 +165,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
                 _apply(sched, which, c, mean)
                 ms = _time(run, reps)
             except sf.SparseFusionError:
-                if c["exec"] not in ("blocks", "ws"):
+                if c["exec"] not in ("blocks", "ws", "tma"):
                     raise
                 continue
             sched.check()

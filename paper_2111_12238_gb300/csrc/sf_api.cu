@@ -85,6 +85,10 @@ struct Dir {
     int *block_seg = nullptr;   // first segment of every block (nb + 1)
     int n_segs = 0, max_seg = 0;
     void *aux = nullptr;        // (c_i, 1 / L_ii) per row, written by the row-block pre-pass
+    // packed records of the row-block order (exec_mode 4), built when that mode is chosen
+    void *pmeta = nullptr, *pvals = nullptr, *paux = nullptr;
+    int *pcols = nullptr;
+    int nvp = 0, packed_B = 0;
     unsigned *flags = nullptr;
     ExecState *st = nullptr;
 };
@@ -154,7 +158,7 @@ sf_status validate_options(const sf_options *o) {
         return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     if (o->block_rows < 0 || o->block_rows > (1 << 20))
         return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
-    if (o->exec_mode < 0 || o->exec_mode > 3) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0, 1, 2 or 3");
+    if (o->exec_mode < 0 || o->exec_mode > 4) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0 .. 4");
     if (o->blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
     if (o->flags & ~(SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE))
         return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
@@ -248,6 +252,28 @@ sf_status block_dir(sf_schedule *S, Dir &d, int B, cudaStream_t s, Arena &tmp) {
                          (d.kind == K_SEP_T) ? &S->MT : nullptr, d.bdesc, s);
     if (e != cudaSuccess) return from_cuda(e, "row-block descriptors");
     d.B = B;
+    d.packed_B = 0;   // packed records follow the block order
+    return SF_OK;
+}
+
+// Packed records of a direction's row-block order (exec_mode 4): allocated once, rebuilt when
+// the block order changes.
+sf_status pack_dir(sf_schedule *S, Dir &d, cudaStream_t s) {
+    if (d.pmeta && d.packed_B == d.B) return SF_OK;
+    const long long nvp = (d.nv + 3) / 4 * 4;
+    if (nvp >= (1LL << 31)) return fail(SF_ERR_UNSUPPORTED, "too many positions for packed records");
+    if (!d.pmeta) {
+        d.pmeta = S->keep.alloc(16 * (size_t)nvp);
+        d.pcols = (int *)S->keep.alloc(sizeof(int) * 8 * (size_t)nvp);
+        d.pvals = S->keep.alloc(sizeof(double) * 8 * (size_t)nvp);
+        d.paux = S->keep.alloc(sizeof(double) * 2 * (size_t)nvp);
+        if (!d.pmeta || !d.pcols || !d.pvals || !d.paux) return fail(SF_ERR_OOM, "packed records: out of device memory");
+    }
+    d.nvp = (int)nvp;
+    SF_CK(pack_pattern(d.kind, d.nv, d.nvp, d.border, d.bdesc, S->L.colidx, S->hasM ? S->M.colidx : nullptr,
+                       S->LT.t.colidx, S->hasMT ? S->MT.t.colidx : nullptr, d.pmeta, d.pcols, s),
+          "packed records");
+    d.packed_B = d.B;
     return SF_OK;
 }
 
@@ -319,6 +345,10 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     if (st != SF_OK) return st;
     d.exec_mode = S->exec_mode;
     d.blpr = d.lpr <= 1 ? 1 : (d.lpr <= 2 ? 2 : (d.lpr <= 16 ? 4 : 32));
+    if (d.exec_mode == 4) {
+        st = pack_dir(S, d, s);
+        if (st != SF_OK) return st;
+    }
     d.present = true;
     return SF_OK;
 }
@@ -490,6 +520,33 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     const int dtype = dt == SF_F64 ? 0 : 1;
     void *vbuf = value_flag_buffer(mode, a);
     const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
+    // row-block executor with packed records and bulk copies
+    if (vf && d.exec_mode == 4 && d.nb > 0) {
+        const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
+        const int rows = std::min(d.B, S->n);
+        const int occ = block_tma_fits(mode, dtype, rows, nc);
+        if (occ <= 0) return fail(SF_ERR_UNSUPPORTED, "row blocks of %d rows do not fit in shared memory", d.B);
+        if (!d.pmeta || d.packed_B != d.B) return fail(SF_ERR_UNSUPPORTED, "packed records are missing");
+        a.aux = d.aux;
+        a.order = d.border;
+        a.bdesc = d.bdesc;
+        a.block_ptr = d.block_ptr;
+        a.seg_ptr = d.seg_ptr;
+        a.block_seg = d.block_seg;
+        a.block_rows = d.B;
+        a.n_blocks = d.nb;
+        a.block_rev = (d.kind == K_PAIRED_T || d.kind == K_SEP_T) ? 1 : 0;
+        a.pack_meta = d.pmeta;
+        a.pack_cols = d.pcols;
+        a.pack_vals = d.pvals;
+        a.pack_aux = d.paux;
+        a.pack_stride = d.nvp;
+        long long blocks = std::min<long long>((long long)occ * S->sms, d.nb);
+        blocks = std::max<long long>(blocks, 1);
+        cudaError_t e = launch_block_tma(mode, dtype, (int)blocks, nc, s, a, d.ev_start, d.ev_stop);
+        if (e != cudaSuccess) return from_cuda(e, "row-block executor launch");
+        return SF_OK;
+    }
     // warp-specialised row-block executor
     if (vf && d.exec_mode == 3 && d.nb > 0) {
         // consumer threads: one per position of the widest segment, a power of two in [32, 256]
@@ -1005,6 +1062,7 @@ SF_API sf_status sf_schedule_replace(sf_schedule *S, int32_t which, int32_t g2_p
         if (st != SF_OK) return st;
         st = block_dir(S, d, d.B, s, tmp);
         if (st != SF_OK) return st;
+        if (d.exec_mode == 4 && (st = pack_dir(S, d, s)) != SF_OK) return st;
     }
     SF_CK(cudaStreamSynchronize(s), "replace");
     return SF_OK;
@@ -1015,7 +1073,7 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
     if (block_rows < 0 || block_rows > (1 << 20)) return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
-    if (exec_mode < -1 || exec_mode > 3) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1, 0, 1, 2 or 3");
+    if (exec_mode < -1 || exec_mode > 4) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1 .. 4");
     if (lanes_per_row != 0 && lanes_per_row != 1 && lanes_per_row != 2 && lanes_per_row != 4 && lanes_per_row != 32)
         return fail(SF_ERR_INVALID_ARG, "row-block lanes per row must be 1, 2, 4 or 32");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
@@ -1031,6 +1089,10 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
         }
         if (exec_mode >= 0) dirs[w]->exec_mode = exec_mode;
         if (lanes_per_row) dirs[w]->blpr = lanes_per_row;
+        if (dirs[w]->exec_mode == 4) {
+            sf_status st = pack_dir(S, *dirs[w], s);
+            if (st != SF_OK) return st;
+        }
     }
     SF_CK(cudaStreamSynchronize(s), "reblock");
     return SF_OK;
@@ -1107,6 +1169,14 @@ SF_API sf_status sf_schedule_debug_swap(sf_schedule *S, int64_t q1, int64_t q2) 
         SF_CK(cudaMemcpy(&b, S->fwd.bdesc + q2, sizeof(int2), cudaMemcpyDeviceToHost), "swap");
         SF_CK(cudaMemcpy(S->fwd.bdesc + q1, &b, sizeof(int2), cudaMemcpyHostToDevice), "swap");
         SF_CK(cudaMemcpy(S->fwd.bdesc + q2, &a, sizeof(int2), cudaMemcpyHostToDevice), "swap");
+    }
+    if (S->fwd.pmeta) {   // packed records follow the block order
+        S->fwd.packed_B = 0;
+        if (S->fwd.exec_mode == 4) {
+            sf_status st = pack_dir(S, S->fwd, 0);
+            if (st != SF_OK) return st;
+            SF_CK(cudaDeviceSynchronize(), "swap");
+        }
     }
     return SF_OK;
 }

@@ -4,6 +4,7 @@
 
 #include "sf_block.cuh"
 #include "sf_block_ws.cuh"
+#include "sf_block_tma.cuh"
 
 namespace sf {
 
@@ -31,6 +32,21 @@ const void *block_ws_kernel_t(int mode) {
     }
 }
 
+// Packed-record row-block kernel (which = 0) or its value-packing pre-pass (which = 1).
+template <typename T>
+const void *block_tma_kernel_t(int mode, int which) {
+    switch (mode) {
+        case M_TRSV_SPMV: return which ? (const void *)k_pack_vals<M_TRSV_SPMV, T> : (const void *)k_block_tma<M_TRSV_SPMV, T>;
+        case M_TRSV: return which ? (const void *)k_pack_vals<M_TRSV, T> : (const void *)k_block_tma<M_TRSV, T>;
+        case M_SPMV_TRSV: return which ? (const void *)k_pack_vals<M_SPMV_TRSV, T> : (const void *)k_block_tma<M_SPMV_TRSV, T>;
+        case M_ADJ_TRSV_SPMV:
+            return which ? (const void *)k_pack_vals<M_ADJ_TRSV_SPMV, T> : (const void *)k_block_tma<M_ADJ_TRSV_SPMV, T>;
+        case M_ADJ_SPMV_TRSV:
+            return which ? (const void *)k_pack_vals<M_ADJ_SPMV_TRSV, T> : (const void *)k_block_tma<M_ADJ_SPMV_TRSV, T>;
+        default: return nullptr;
+    }
+}
+
 // lpr == 0 selects the pre-pass of the mode.
 template <typename T>
 const void *block_kernel_t(int mode, int lpr) {
@@ -50,5 +66,7 @@ const void *block_kernel_f64(int mode, int lpr);
 const void *block_kernel_f32(int mode, int lpr);
 const void *block_ws_kernel_f64(int mode);
 const void *block_ws_kernel_f32(int mode);
+const void *block_tma_kernel_f64(int mode, int which);
+const void *block_tma_kernel_f32(int mode, int which);
 
 }  // namespace sf

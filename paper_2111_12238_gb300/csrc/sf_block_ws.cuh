@@ -139,6 +139,7 @@ struct WsChunks {
     int s, s1;        // current segment and the block's end segment
     int q0, q1;       // current chunk's positions
     int seg_end;      // end position of the current segment
+    int next_end;     // end position of the next segment (loaded one segment ahead)
     bool new_block;   // the current chunk opens a block
     __device__ bool first(const ExecArgs &a, int nc) {
         b = blockIdx.x;
@@ -153,6 +154,7 @@ struct WsChunks {
             if (s < s1) {
                 q0 = __ldg(a.seg_ptr + s);
                 seg_end = __ldg(a.seg_ptr + s + 1);
+                next_end = __ldg(a.seg_ptr + min(s + 2, s1));
                 q1 = min(seg_end, q0 + nc);
                 new_block = true;
                 return true;
@@ -169,7 +171,8 @@ struct WsChunks {
         }
         if (++s < s1) {
             q0 = seg_end;
-            seg_end = __ldg(a.seg_ptr + s + 1);
+            seg_end = next_end;
+            next_end = __ldg(a.seg_ptr + min(s + 2, s1));   // used one segment later
             q1 = min(seg_end, q0 + nc);
             return true;
         }

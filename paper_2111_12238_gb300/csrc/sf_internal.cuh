@@ -75,6 +75,12 @@ struct ExecArgs {
     void *y, *xs, *gb, *gx, *gL, *gM;
     void *aux;                          // row-block executor: (c_i, 1 / L_ii) per row
     const void *rdiag;                  // 1 / L_ii per row (k = 1 value-flag launches), or NULL
+    // packed records of the row-block order (exec_mode 4): structures of arrays, stride pack_stride
+    const void *pack_meta;              // (order entry, first entry, end) per position
+    const int *pack_cols;               // first kTmaU column indices per position
+    void *pack_vals;                    // their values (gathered every call)
+    void *pack_aux;                     // (c_i, 1 / L_ii) per position (gathered every call)
+    int pack_stride;
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
@@ -95,6 +101,14 @@ size_t block_exec_smem(int mode, int dtype, int block_rows);
 // Warp-specialised row-block executor: nc consumer threads (32, 64, 128 or 256) plus
 // 512 producer threads; resident CTAs per SM (0: does not fit) and launch.
 int block_ws_fits(int mode, int dtype, int rows, int nc);
+// Row-block executor with packed records and bulk copies (exec_mode 4): nc consumer threads
+// (32, 64, 128 or 256) plus one producer warp. pack_pattern writes the pattern part of the
+// packed records (stride nvp = nv rounded up to 4; positions past nv are padding).
+cudaError_t pack_pattern(int kind, long long nv, int nvp, const int *border, const int2 *bdesc, const int *Lci,
+                         const int *Mci, const int *LTci, const int *MTci, void *meta, int *cols, cudaStream_t s);
+int block_tma_fits(int mode, int dtype, int rows, int nc);
+cudaError_t launch_block_tma(int mode, int dtype, int blocks, int nc, cudaStream_t s, const ExecArgs &a,
+                             cudaEvent_t ev_start, cudaEvent_t ev_stop);
 cudaError_t launch_block_ws(int mode, int dtype, int blocks, int nc, cudaStream_t s, const ExecArgs &a,
                             cudaEvent_t ev_start, cudaEvent_t ev_stop);
 // Pre-pass of partition launches with value flags: resets vec[0..n) to the all-ones pattern

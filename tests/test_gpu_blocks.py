@@ -154,17 +154,18 @@ def test_block_executor_timeout_is_reported():
 # ---- warp-specialised row-block executor (exec_mode 3): producer warps stage each level's
 # records in shared memory, consumer warps only compute
 
+@pytest.mark.parametrize("mode", [3, 4])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("B", [64, 1000, 8192])
 @pytest.mark.parametrize("g2", [0, -1])
-def test_ws_trsv_spmv_forward_adjoint(dtype, B, g2):
+def test_ws_trsv_spmv_forward_adjoint(mode, dtype, B, g2):
     need_cuda()
     w = _work("trsv_spmv")
     x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
     gb_ref, gL_ref, gM_ref = oracle.adj_trsv_spmv(w.L, w.M, x_ref, w.gy)
-    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, block_rows=B, exec_mode=3,
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, block_rows=B, exec_mode=mode,
                      g2_placement=g2)
-    assert sch.info()["exec_mode"] == 3
+    assert sch.info()["exec_mode"] == mode
     Lv, Mv, b, gy = t(w.L.vals, dtype), t(w.M.vals, dtype), t(w.b, dtype), t(w.gy, dtype)
     xs = torch.empty_like(b)
     for _ in range(2):
@@ -179,14 +180,15 @@ def test_ws_trsv_spmv_forward_adjoint(dtype, B, g2):
     assert vec_rel_err(host(gL), gL_ref) < tol and vec_rel_err(host(gM), gM_ref) < tol
 
 
+@pytest.mark.parametrize("mode", [3, 4])
 @pytest.mark.parametrize("B", [512, 9000])
-def test_ws_spmv_trsv_forward_adjoint(B):
+def test_ws_spmv_trsv_forward_adjoint(mode, B):
     # long A rows (power-law lengths up to 120) exercise the entries beyond the staged eight
     need_cuda()
     w = _work("spmv_trsv")
     z_ref = oracle.spmv_trsv(w.M, w.L, w.x_in, w.b)
     gb_ref, gx_ref, gL_ref, gA_ref = oracle.adj_spmv_trsv(w.M, w.L, w.x_in, z_ref, w.gy)
-    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, block_rows=B, exec_mode=3)
+    sch = sf.inspect("spmv_trsv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True, block_rows=B, exec_mode=mode)
     Lv, Av, xin = t(w.L.vals), t(w.M.vals), t(w.x_in)
     z = sch.execute(Lv, Av, b=t(w.b), x_in=xin)
     gx, gL, gA = torch.empty_like(xin), torch.empty_like(Lv), torch.empty_like(Av)
@@ -197,7 +199,8 @@ def test_ws_spmv_trsv_forward_adjoint(B):
     assert vec_rel_err(host(gL), gL_ref) < 1e-12 and vec_rel_err(host(gA), gA_ref) < 1e-12
 
 
-def test_ws_trsv_integer_exact_and_batched():
+@pytest.mark.parametrize("mode", [3, 4])
+def test_ws_trsv_integer_exact_and_batched(mode):
     need_cuda()
     n = 5000
     pat = I.powerlaw_lower(n, 3, 12, 77)
@@ -206,13 +209,13 @@ def test_ws_trsv_integer_exact_and_batched():
     x_int = (np.arange(n) % 5 - 2).astype(np.float64).reshape(n, 1)
     b = oracle.spmv(L, x_int)
     for B in (128, 8192):
-        sch = sf.inspect("trsv", dev_csr(L), block_rows=B, exec_mode=3)
+        sch = sf.inspect("trsv", dev_csr(L), block_rows=B, exec_mode=mode)
         x = sch.execute(t(L.vals), b=t(b))
         sch.check()
         assert np.array_equal(host(x), x_int)
     wb = I.batched_trsv_spmv(count=10, nmin=300, nmax=9000, seed=12)
     sb = sf.inspect_batched("trsv_spmv", [dev_csr(x.L) for x in wb.instances], [dev_csr(x.M) for x in wb.instances],
-                            want_adjoint=True, block_rows=4096, exec_mode=3)
+                            want_adjoint=True, block_rows=4096, exec_mode=mode)
     Lb = t(np.concatenate([x.L.vals for x in wb.instances]))
     Mb = t(np.concatenate([x.M.vals for x in wb.instances]))
     xs = torch.empty_like(t(wb.b))
@@ -228,12 +231,13 @@ def test_ws_trsv_integer_exact_and_batched():
         off += x.n
 
 
-def test_ws_timeout_is_reported():
+@pytest.mark.parametrize("mode", [3, 4])
+def test_ws_timeout_is_reported(mode):
     # a row placed in a level segment before its input: the bounded wait ends the launch
     need_cuda()
     n = 64
     L = dense_to_csr(np.eye(n) * 2 + np.eye(n, k=-1))
-    sch = sf.inspect("trsv", dev_csr(L), block_rows=64, exec_mode=3)
+    sch = sf.inspect("trsv", dev_csr(L), block_rows=64, exec_mode=mode)
     sch.set_timeout(2_000_000)
     sch.debug_swap(0, 32)
     Lv, bb = t(L.vals), t(np.ones((n, 1)))
@@ -244,3 +248,18 @@ def test_ws_timeout_is_reported():
     x = sch.execute(Lv, b=bb)
     sch.check()
     assert col_rel_err(host(x), oracle.trsv_lower(L, np.ones((n, 1)))) < 1e-14
+
+
+def test_tma_reblock_and_replace_repack():
+    # the packed records follow the block order through re-blocking and re-placement
+    need_cuda()
+    w = _work("trsv_spmv")
+    x_ref, y_ref = oracle.trsv_spmv(w.L, w.M, w.b)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), block_rows=1000)
+    Lv, Mv, b = t(w.L.vals), t(w.M.vals), t(w.b)
+    for B, g2 in ((1000, 0), (4096, 0), (4096, -1), (512, 3)):
+        sch.reblock(0, B, 4, 0)
+        sch.replace(0, g2)
+        y = sch.execute(Lv, Mv, b=b)
+        sch.check()
+        assert col_rel_err(host(y), y_ref) < 1e-12

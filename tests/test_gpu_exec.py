@@ -246,8 +246,9 @@ def test_recut_and_autotune_keep_results_exact():
         if r["exec"] == "blocks":
             assert inf[pre + "exec_mode"] == 2 and inf[pre + "block_lanes"] == r["block_lanes"]
             assert inf[pre + "block_rows"] == r["block_rows"]
-        elif r["exec"] == "ws":
-            assert inf[pre + "exec_mode"] == 3 and inf[pre + "block_rows"] == r["block_rows"]
+        elif r["exec"] in ("ws", "tma"):
+            assert inf[pre + "exec_mode"] == (3 if r["exec"] == "ws" else 4)
+            assert inf[pre + "block_rows"] == r["block_rows"]
         else:
             assert inf[pre + "exec_mode"] == 1 and r["lanes"] in autotune.DEFAULT_LANES
             assert inf[pre + "lanes_per_row"] == r["lanes"]

@@ -438,7 +438,6 @@ def run_gpu(args):
         return
     hbm, peak_src = _peaks()
     info = g.sched.info()
-    pre = int(wl["k"] == 1 and wl["pair"] != "ic0_trsv")   # pre-pass of value-flag launches
     # dominant kernel: the longer of the fused forward and fused adjoint executor kernels
     dom = "fwd" if (1 not in exec_ms or exec_ms[0] >= exec_ms[1]) else "adj"
     dom_ms = exec_ms[0] if dom == "fwd" else exec_ms[1]
@@ -506,10 +505,9 @@ def run_gpu(args):
         "tuned": tuned,
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        # per forward: the pre-pass (value-flag reset and 1 / L_ii, one right-hand side only)
-        # and the fused kernel; per adjoint: two value gathers, the pre-pass, the fused kernel
-        # and two gradient passes
-        "gpu_launches": args.steps * ((1 + pre) + ((5 + pre) if wl["adj"] else 0)),
+        # our kernels per step, as the library counts them for the tuned launch shapes:
+        # pre-passes, value gathers, fused kernels and gradient passes
+        "gpu_launches": args.steps * (g.sched.launches(0, wl["k"]) + (g.sched.launches(1, wl["k"]) if wl["adj"] else 0)),
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

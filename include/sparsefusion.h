@@ -265,6 +265,11 @@ sf_status sf_schedule_replace(sf_schedule *sch, int32_t which, int32_t g2_placem
 sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,
                               int32_t lanes_per_row, void *stream);
 
+/* Number of kernel launches one sf_execute (which = 0) or one sf_adjoint with both value
+ * gradients (which = 1) makes with k right-hand sides in the schedule's current launch shape
+ * (pre-passes, gathers and gradient passes included). Host only. */
+sf_status sf_schedule_launches(const sf_schedule *sch, int32_t which, int32_t k, int32_t *count);
+
 /* Timing hook: the next launches of the forward (0) or adjoint (1) schedule record ev_start
  * (a cudaEvent_t) on the launch stream right before the fused executor kernel and ev_stop
  * right after it (pre-passes, gathers and gradient passes fall outside), so a caller can

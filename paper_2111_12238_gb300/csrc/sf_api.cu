@@ -802,9 +802,12 @@ SF_API sf_status sf_adjoint(const sf_schedule *S, sf_dtype dt, int32_t k, const 
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int dtype = dt == SF_F64 ? 0 : 1;
-    // 1. values of L^T and M^T (A^T) in transposed order, one coalesced gather each
+    // 1. values of L^T and M^T (A^T) in transposed order, one coalesced gather each; the
+    //    row-block executors of the SpTRSV -> SpMV adjoint read M^T only in their pre-pass
+    //    (u = M^T gy), which then reads M's values through the permutation instead
+    a.mt_direct = (mode == M_ADJ_TRSV_SPMV && k == 1 && !S->epoch_flags && S->adj.exec_mode >= 2) ? 1 : 0;
     SF_CK(launch_gather_vals(dtype, S->L.nnz, S->LT.perm, L_vals, S->LTv, s), "adjoint gather");
-    SF_CK(launch_gather_vals(dtype, S->M.nnz, S->MT.perm, M_vals, S->MTv, s), "adjoint gather");
+    if (!a.mt_direct) SF_CK(launch_gather_vals(dtype, S->M.nnz, S->MT.perm, M_vals, S->MTv, s), "adjoint gather");
     // 2. the fused pass on the transposed schedule
     sf_status st = launch(S, S->adj, mode, dt, k, a, s);
     if (st != SF_OK) return st;
@@ -1095,6 +1098,25 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
         }
     }
     SF_CK(cudaStreamSynchronize(s), "reblock");
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_launches(const sf_schedule *S, int32_t which, int32_t k, int32_t *count) {
+    if (!S || !count) return fail(SF_ERR_INVALID_ARG, "schedule or count is NULL");
+    if (which != 0 && which != 1) return fail(SF_ERR_INVALID_ARG, "which must be 0 or 1");
+    if (k < 1) return fail(SF_ERR_INVALID_ARG, "k must be >= 1");
+    const Dir &d = which ? S->adj : S->fwd;
+    if (!d.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    const bool vf_pair = S->pair == SF_TRSV_SPMV || S->pair == SF_SPMV_TRSV || S->pair == SF_TRSV;
+    const bool vf = k == 1 && !S->epoch_flags && vf_pair;
+    int n = 0;
+    if (vf && d.exec_mode >= 2 && d.nb > 0) n = 2 + (d.exec_mode == 4 ? 1 : 0);   // pre-pass(es) + executor
+    else n = (vf ? 1 : 0) + 1;                                                  // value-flag reset + executor
+    if (which == 1) {
+        const bool mt_direct = S->pair == SF_TRSV_SPMV && vf && d.exec_mode >= 2;
+        n += 1 + (mt_direct ? 0 : 1) + 2;   // value gathers and both gradient passes
+    }
+    *count = n;
     return SF_OK;
 }
 

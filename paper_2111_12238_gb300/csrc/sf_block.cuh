@@ -113,6 +113,10 @@ __global__ void __launch_bounds__(256) k_block_prep(const ExecArgs a) {
             const int *ci = MODE == M_SPMV_TRSV ? a.Mci : a.MTci;
             const T *vals = (const T *)(MODE == M_SPMV_TRSV ? a.Mv : a.MTv);
             const T *src = (const T *)(MODE == M_SPMV_TRSV ? a.xin : a.gy);
+            // M^T's values straight from M through the transpose permutation when the
+            // adjoint skipped their gather
+            const int *perm = (MODE == M_ADJ_TRSV_SPMV && a.mt_direct) ? a.MTperm : nullptr;
+            const T *mv = (const T *)a.Mv;
             const int e0 = __ldg(rp + i), e1 = __ldg(rp + i + 1);
             T acc = T(0);
             for (int e = e0; e < e1; e += kUnroll) {
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(256) k_block_prep(const ExecArgs a) {
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     j[u] = e + u < e1 ? __ldg(ci + e + u) : -1;
-                    v[u] = e + u < e1 ? __ldg(vals + e + u) : T(0);
+                    v[u] = e + u < e1 ? (perm ? __ldg(mv + __ldg(perm + e + u)) : __ldg(vals + e + u)) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u)

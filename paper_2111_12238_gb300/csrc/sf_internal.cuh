@@ -75,6 +75,7 @@ struct ExecArgs {
     void *y, *xs, *gb, *gx, *gL, *gM;
     void *aux;                          // row-block executor: (c_i, 1 / L_ii) per row
     const void *rdiag;                  // 1 / L_ii per row (k = 1 value-flag launches), or NULL
+    int mt_direct;                      // row-block pre-pass reads M's values through MTperm (no MTv)
     // packed records of the row-block order (exec_mode 4): structures of arrays, stride pack_stride
     const void *pack_meta;              // (order entry, first entry, end) per position
     const int *pack_cols;               // first kTmaU column indices per position

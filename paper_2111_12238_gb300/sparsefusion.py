@@ -95,6 +95,7 @@ _SIGS = {
     "sf_schedule_replace": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "sf_schedule_set_occupancy": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_set_exec_events": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "sf_schedule_launches": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
@@ -299,6 +300,13 @@ class Schedule:
                "sf_schedule_export_blocks")
         return dict(order=order, block_ptr=bp, seg_ptr=sp, block_seg=bs,
                     block_rows=inf["block_rows"] if which == 0 else inf["adj_block_rows"])
+
+    def launches(self, which=0, k=1) -> int:
+        """Kernel launches of one execute (0) or adjoint with both gradients (1)."""
+        n = C.c_int32(0)
+        _check(load_library().sf_schedule_launches(self.handle, int(which), int(k), C.byref(n)),
+               "sf_schedule_launches")
+        return n.value
 
     def set_exec_events(self, which, start=None, stop=None):
         """Records torch.cuda.Event pair (start, stop) around the next launches of the fused

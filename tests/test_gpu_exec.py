@@ -374,3 +374,15 @@ def test_occupancy_variants_are_exact(lanes):
     x = s2.execute(Lv, b=b)
     s2.check()
     assert col_rel_err(host(x), x_ref) < 1e-12
+
+
+def test_launch_counts():
+    need_cuda()
+    w = _lap3d(10, 1)
+    sch = sf.inspect("trsv_spmv", dev_csr(w.L), dev_csr(w.M), want_adjoint=True)
+    assert sch.launches(0, 1) == 2 and sch.launches(1, 1) == 6       # reset + executor; gathers, reset, executor, grads
+    assert sch.launches(0, 4) == 1 and sch.launches(1, 4) == 5       # epoch flags for k > 1
+    sch.reblock(-1, 512, 3, 0)
+    assert sch.launches(0, 1) == 2 and sch.launches(1, 1) == 5       # pre-pass + executor; one gather
+    sch.reblock(-1, 512, 4, 0)
+    assert sch.launches(0, 1) == 3 and sch.launches(1, 1) == 6       # pre-pass + packing + executor

@@ -332,8 +332,10 @@ def run_gpu(args):
     launch_opts = dict(lanes_per_row=args.lanes, blocks_per_sm=args.blocks_per_sm, epoch_flags=args.epoch_flags,
                        part_cost_target=args.part_cost, dynamic_queue=args.dynamic_queue,
                        rhs_tile=kt if wl["k"] > 1 else 0, team_lanes=args.team, block_rows=args.block_rows,
-                       exec_mode=args.exec_mode)
+                       exec_mode=args.exec_mode, g2_placement=args.g2)
     g = Gpu(wl, args.dtype, device, launch_opts)
+    if wl["adj"] and args.adj_exec_mode >= 0:
+        g.sched.reblock(1, args.adj_block_rows, args.adj_exec_mode, 0)
     fns = [g.fwd] + ([g.adj] if wl["adj"] else [])
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device) if wl["fits_l2"] else None
     flush = (lambda: flush_buf.zero_()) if flush_buf is not None else None
@@ -597,7 +599,12 @@ def main():
     ap.add_argument("--dynamic-queue", action="store_true", help="draw partitions from a ticket counter")
     ap.add_argument("--team", type=int, default=0, help="lanes per partition team: 8 or 32 (0 = auto)")
     ap.add_argument("--block-rows", type=int, default=0, help="rows per block of the row-block executor")
-    ap.add_argument("--exec-mode", type=int, default=0, help="0 auto, 1 partitions, 2 row blocks")
+    ap.add_argument("--exec-mode", type=int, default=0,
+                    help="0 auto, 1 partitions, 2 row blocks, 3 warp-specialised row blocks, 4 packed row blocks")
+    ap.add_argument("--g2", type=int, default=0,
+                    help="placement of second-kernel rows: 0 earliest wavefront, -1 last, d > 0 delayed by d")
+    ap.add_argument("--adj-exec-mode", type=int, default=-1, help="executor of the adjoint pass (-1: as --exec-mode)")
+    ap.add_argument("--adj-block-rows", type=int, default=0, help="rows per block of the adjoint's row blocks")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the default launch shape)")
     ap.add_argument("--tune-seconds", type=float, default=8.0, help="time budget of each autotuning search")
     args = ap.parse_args()

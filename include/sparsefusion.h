@@ -219,6 +219,9 @@ typedef struct {
     int32_t split_pct, adj_split_pct;             /* see sf_schedule_set_split */
     int32_t g2_placement, adj_g2_placement;       /* see sf_options.g2_placement */
     int32_t min_blocks, adj_min_blocks;           /* see sf_schedule_set_occupancy */
+    int64_t ic0_pairs;                 /* IC0 schedules: intersection pairs listed by the
+                                          inspector (-1: too many, not listed); else 0 */
+    int32_t ic0_use_pairs, reserved3;  /* 1 when the factor reads the listed pairs */
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -280,11 +283,21 @@ sf_status sf_schedule_set_exec_events(sf_schedule *sch, int32_t which, void *ev_
 /* Register budget of the partition executor's kernels for the forward (0), adjoint (1) or
  * both (-1) schedules: min_blocks 1 (or 0, the default) lets the kernels keep all the
  * registers they want, which suits schedules bound by their dependence chain; 3 selects
- * variants compiled for three resident 256-thread blocks per SM (85 registers), which suits
- * schedules bound by the number of rows in flight (many independent instances). The
- * variants exist for value-flag launches (k = 1) with 1, 2 or 4 lanes per row and 32-lane
- * teams; other launches use the default kernels. No GPU work. */
+ * variants compiled for three (four for IC0) resident 256-thread blocks per SM, which suits
+ * schedules bound by the number of rows in flight (many independent instances, wide
+ * wavefronts). The variants exist for value-flag launches (k = 1) with 1, 2 or 4 lanes per
+ * row and 32-lane teams, and for IC0 launches with 32 lanes per row; other launches use the
+ * default kernels. No GPU work. */
 sf_status sf_schedule_set_occupancy(sf_schedule *sch, int32_t which, int32_t min_blocks);
+
+/* IC0 schedules (SF_IC0_TRSV, SF_IC0; §2.1 up-looking zero-fill factor): entry (i, j) of
+ * the factor subtracts sum_{k<j} L_ik L_jk over the columns k that rows i and j share. The
+ * inspector lists those columns once per entry as pairs of entry positions (8 bytes per
+ * pair, kept with the schedule) unless there are more than 4 nnz(L) + 2^20 of them. use = 1
+ * (the default when listed) makes the executor read the pairs; with use = 0 it finds the
+ * common columns by binary search on every call. SF_ERR_UNSUPPORTED for other pairs, or
+ * for use = 1 when nothing was listed. No GPU work. */
+sf_status sf_schedule_set_ic0_pairs(sf_schedule *sch, int32_t use);
 
 /* Partition classes of the separated schedules (SpTRSV -> SpMV forward, SpMV -> SpTRSV
  * adjoint): with class0_pct in 1..99 that percent of the executor's teams run the partitions

@@ -25,7 +25,7 @@ import torch
 from . import sparsefusion as sf
 
 DEFAULT_LANES = (1, 2, 4, 8, 16, 32)
-DEFAULT_ITEMS = (2, 4, 8, 16, 32)
+DEFAULT_ITEMS = (1, 2, 4, 8, 16, 32)
 DEFAULT_TEAMS = (8, 32)
 DEFAULT_BLOCK_ROWS = (1024, 2048, 4096, 8192, 16384)
 DEFAULT_BLOCK_LANES = (1, 2, 4, 32)
@@ -173,7 +173,10 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
             if ms < best["ms"]:
                 best = trials[-1]
     # the best partition shape on the occupancy variants of the executor kernels
-    if best is not None and best["exec"] == "partitions" and k == 1 and occupancy and best.get("lanes", 32) <= 4:
+    ic0 = sched.pair in ("ic0", "ic0_trsv")
+    occ_variant = (k == 1 and best is not None and best.get("lanes", 32) <= 4) or \
+        (ic0 and best is not None and best.get("lanes") == 32 and best.get("team") == 32)
+    if best is not None and best["exec"] == "partitions" and occupancy and occ_variant:
         c = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2")}
         c["occ"] = 3
         _apply(sched, which, c, mean)

@@ -138,6 +138,12 @@ struct sf_schedule {
     unsigned long long timeout_ns = 2000000000ull;
     double reuse = 0.0, inspect_ms = 0.0;
     int packing = 0;
+    // IC0 intersection pairs listed by the inspector (NULL when there were too many)
+    int *ic0_pp = nullptr;
+    int2 *ic0_pairs = nullptr;
+    long long ic0_npairs = 0;
+    bool ic0_use_pairs = true;
+    void *ic0_rinv = nullptr;   // 1 / L_ii of the factor, n values of the widest element type
     std::mutex mu;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -398,6 +404,14 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
     S->packing = (kind == K_SEP) ? 0 : 1;
     sf_status st = build_dir(S, S->fwd, kind, what, o.part_cost_target, s, tmp);
     if (st != SF_OK) return st;
+    if (S->pair == SF_IC0_TRSV || S->pair == SF_IC0) {
+        // room for four pairs per entry on average before the factor searches per call
+        const long long cap = 4 * S->L.nnz + (1LL << 20);
+        SF_CK(build_ic0_pairs(S->L, cap, &S->ic0_pp, &S->ic0_pairs, &S->ic0_npairs, s, tmp, S->keep),
+              "inspector: IC0 intersection pairs");
+        S->ic0_rinv = S->keep.alloc(sizeof(double) * (size_t)std::max(S->n, 1));
+        if (S->keep.oom || !S->ic0_rinv) return fail(SF_ERR_OOM, "inspector: out of device memory");
+    }
     if (want_adj) {
         if (S->pair == SF_TRSV_SPMV) st = build_dir(S, S->adj, K_PAIRED_T, 1, o.part_cost_target, s, tmp);
         else st = build_dir(S, S->adj, K_SEP_T, 2, o.part_cost_target, s, tmp);
@@ -517,6 +531,9 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     a.MTrp = S->hasMT ? S->MT.t.rowptr : nullptr;
     a.MTci = S->hasMT ? S->MT.t.colidx : nullptr;
     a.MTperm = S->hasMT ? S->MT.perm : nullptr;
+    a.ic0_pp = S->ic0_use_pairs ? S->ic0_pp : nullptr;
+    a.ic0_pairs = S->ic0_use_pairs ? S->ic0_pairs : nullptr;
+    a.ic0_rinv = S->ic0_rinv;
     const int dtype = dt == SF_F64 ? 0 : 1;
     void *vbuf = value_flag_buffer(mode, a);
     const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
@@ -969,6 +986,8 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     info->adj_g2_placement = S->adj.g2;
     info->min_blocks = S->fwd.minb;
     info->adj_min_blocks = S->adj.minb;
+    info->ic0_pairs = (S->pair == SF_IC0_TRSV || S->pair == SF_IC0) ? (S->ic0_pp ? S->ic0_npairs : -1) : 0;
+    info->ic0_use_pairs = (S->ic0_pp && S->ic0_use_pairs) ? 1 : 0;
     info->block_segments = S->fwd.n_segs;
     info->adj_block_segments = S->adj.n_segs;
     info->block_threads = S->fwd.present ? block_threads(S->fwd) : 0;
@@ -1139,6 +1158,15 @@ SF_API sf_status sf_schedule_set_occupancy(sf_schedule *S, int32_t which, int32_
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w)
         if ((which == -1 || which == w) && dirs[w]->present) dirs[w]->minb = min_blocks ? min_blocks : 1;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_ic0_pairs(sf_schedule *S, int32_t use) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (use != 0 && use != 1) return fail(SF_ERR_INVALID_ARG, "use must be 0 or 1");
+    if (S->pair != SF_IC0_TRSV && S->pair != SF_IC0) return fail(SF_ERR_UNSUPPORTED, "not an IC0 schedule");
+    if (use && !S->ic0_pp) return fail(SF_ERR_UNSUPPORTED, "no intersection pairs were listed for this schedule");
+    S->ic0_use_pairs = use != 0;
     return SF_OK;
 }
 

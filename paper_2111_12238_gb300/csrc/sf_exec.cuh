@@ -337,27 +337,12 @@ __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int g
     return ok;
 }
 
-// Paired SpIC0 -> SpTRSV row (combination 5, F = I), IC0 in its up-looking row form:
-// for each j < i in row i, ascending, L_ij = (A_ij - sum_{k<j, k in both rows} L_ik L_jk)
-// / L_jj; then L_ii = sqrt(A_ii - sum_{k<i} L_ik^2); then the solve row with the fresh
-// L_i on chip: y_i = (b_i - sum_j L_ij y_j) / L_ii. Factor values go to a.xs.
-template <typename T, int LPR, bool SOLVE>
-__device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
-    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+// Factor entries of IC0 row i (up-looking form, §2.1) with the common columns found by a
+// binary search of row i for every column of row j; returns sum_{k<i} L_ik^2 on every lane.
+template <typename T, int LPR>
+__device__ __forceinline__ T ic0_row_search(const ExecArgs &a, int rs, int dg, int gl, unsigned gmask) {
     const T *Av = (const T *)a.Lv;
     T *lf = (T *)a.xs;
-    bool ok = true;
-    // every predecessor row publishes its factor row and its solve row together
-    for (int e = rs + gl; e < dg; e += LPR * kUnroll) {
-        int j[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int ee = e + u * LPR;
-            j[u] = ee < dg ? __ldg(a.Lci + ee) : -1;
-        }
-        if (ok) ok = wait_flags<kUnroll>(a.flags, j, epoch, a.st, a.timeout_ns, row);
-    }
-    ok = group_ok<LPR>(ok, gmask);
     for (int t = rs; t < dg; ++t) {
         const int jr = __ldg(a.Lci + t);
         const int js = __ldg(a.Lrp + jr), jd = __ldg(a.Lrp + jr + 1) - 1;
@@ -380,11 +365,129 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
         const T v = lf[t];
         sq += v * v;
     }
-    sq = group_sum<LPR>(sq, gmask);
-    const T dd = __ldg(Av + dg) - sq;
+    return group_sum<LPR>(sq, gmask);
+}
+
+// Factor entries of IC0 row i with the inspector's intersection pairs (a.ic0_pp/ic0_pairs):
+// lanes take one entry each. An entry without pairs depends on no other entry of its row
+// (L_ij = A_ij / L_jj), so those finish side by side; entries with pairs follow one at a time
+// in increasing column order, the group summing their pair products. 1 / L_jj comes from the
+// table the rows publish with their factor (a.ic0_rinv), so an entry costs one multiply. The
+// first chunk's pattern and A values (j0, q0, q1, av0) were loaded before the wait. Returns
+// sum_{k<i} L_ik^2 on every lane; the sum runs over the lanes that hold entries only.
+template <typename T, int LPR>
+__device__ __forceinline__ T ic0_row_pairs(const ExecArgs &a, int rs, int dg, int gl, unsigned gmask, int j0, int q0,
+                                           int q1, T av0) {
+    const T *Av = (const T *)a.Lv;
+    const T *rinv = (const T *)a.ic0_rinv;
+    T *lf = (T *)a.xs;
+    const int gbase = (int)(threadIdx.x & 31) - gl;
+    T sq = T(0);
+    for (int c0 = rs; c0 < dg; c0 += LPR) {
+        const int t = c0 + gl;
+        const bool mine = t < dg;
+        int j = j0, p0 = q0, p1 = q1;
+        T av = av0;
+        if (c0 != rs && mine) {
+            j = __ldg(a.Lci + t);
+            p0 = __ldg(a.ic0_pp + t);
+            p1 = __ldg(a.ic0_pp + t + 1);
+            av = __ldg(Av + t);
+        }
+        const T rj = mine ? __ldcg(rinv + j) : T(0);
+        T v = T(0);
+        if (mine && p0 == p1) {
+            v = av * rj;
+            lf[t] = v;
+        }
+        unsigned serial = __ballot_sync(gmask, mine && p0 < p1);
+        if (serial) {
+            __syncwarp(gmask);
+            while (serial) {
+                const int src = __ffs(serial) - 1;
+                serial &= serial - 1;
+                const int s0 = __shfl_sync(gmask, p0, src), s1 = __shfl_sync(gmask, p1, src);
+                T part = T(0);
+                for (int g = s0 + gl; g < s1; g += LPR) {
+                    const int2 pq = __ldg(a.ic0_pairs + g);
+                    part += lf[pq.x] * __ldcg(lf + pq.y);
+                }
+                part = group_sum<LPR>(part, gmask);
+                if (gl == src - gbase) {
+                    v = (av - part) * rj;
+                    lf[t] = v;
+                }
+                __syncwarp(gmask);
+            }
+        }
+        sq += v * v;
+    }
+    const int w = dg - rs;   // lanes at or past w hold no entry
+#pragma unroll
+    for (int off = LPR / 2; off >= 1; off >>= 1)
+        if (off < w) sq += __shfl_xor_sync(gmask, sq, off);
+    return __shfl_sync(gmask, sq, gbase);
+}
+
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+// Paired SpIC0 -> SpTRSV row (combination 5, F = I), IC0 in its up-looking row form:
+// for each j < i in row i, ascending, L_ij = (A_ij - sum_{k<j, k in both rows} L_ik L_jk)
+// / L_jj; then L_ii = sqrt(A_ii - sum_{k<i} L_ik^2); then the solve row with the fresh
+// L_i on chip: y_i = (b_i - sum_j L_ij y_j) / L_ii. Factor values go to a.xs; 1 / L_ii goes
+// to a.ic0_rinv with them (one reciprocal square root gives both L_ii and 1 / L_ii).
+template <typename T, int LPR, bool SOLVE>
+__device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
+    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+    const T *Av = (const T *)a.Lv;
+    T *lf = (T *)a.xs;
+    // pattern-only operands of the first chunk, loaded before the wait
+    int j0 = 0, q0 = 0, q1 = 0;
+    T av0 = T(0);
+    if (a.ic0_pp && rs + gl < dg) {
+        j0 = __ldg(a.Lci + rs + gl);
+        q0 = __ldg(a.ic0_pp + rs + gl);
+        q1 = __ldg(a.ic0_pp + rs + gl + 1);
+        av0 = __ldg(Av + rs + gl);
+    }
+    const T aii = __ldg(Av + dg);
+    bool ok = true;
+    // every predecessor row publishes its factor row and its solve row together
+    for (int e = rs + gl; e < dg; e += LPR * kUnroll) {
+        int j[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int ee = e + u * LPR;
+            j[u] = ee < dg ? __ldg(a.Lci + ee) : -1;
+        }
+        if (ok) ok = wait_flags<kUnroll>(a.flags, j, epoch, a.st, a.timeout_ns, row);
+    }
+    ok = group_ok<LPR>(ok, gmask);
+    // The solve's first column tile of y over the row's first entries does not depend on the
+    // factor: it is loaded before the factor row is computed.
+    constexpr int kY = 4;
+    T yv[kY];
+    T bv = T(0);
+    if (SOLVE) {
+        const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
+        const T *y = (const T *)a.y;
+#pragma unroll
+        for (int u = 0; u < kY; ++u) {
+            const int t = rs + s + u * S;
+            yv[u] = (cl < k && t < dg) ? __ldcg(y + (size_t)__ldg(a.Lci + t) * k + cl) : T(0);
+        }
+        if (s == 0 && cl < k) bv = __ldg((const T *)a.b + (size_t)row * k + cl);
+    }
+    const T sq = a.ic0_pp ? ic0_row_pairs<T, LPR>(a, rs, dg, gl, gmask, j0, q0, q1, av0)
+                          : ic0_row_search<T, LPR>(a, rs, dg, gl, gmask);
+    const T dd = aii - sq;
     if (gl == 0 && !(dd > T(0))) record_error(a.st, SF_ERR_BREAKDOWN, row);
-    const T lii = sqrt(dd);
-    if (gl == 0) lf[dg] = lii;
+    const T ri = rsqrt_t(dd);
+    if (gl == 0) {
+        lf[dg] = dd * ri;
+        ((T *)a.ic0_rinv)[row] = ri;
+    }
     if (SOLVE) {
         const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
         const T *b = (const T *)a.b;
@@ -393,11 +496,17 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
         for (int c0 = 0; c0 < k; c0 += kt) {
             const int c = c0 + cl;
             T acc = T(0);
+            int t = rs + s;
+            if (c0 == 0) {
+#pragma unroll
+                for (int u = 0; u < kY; ++u)
+                    if (t + u * S < dg) acc += lf[t + u * S] * yv[u];
+                t += kY * S;
+            }
             if (c < k)
-                for (int t = rs + s; t < dg; t += S)
-                    acc += lf[t] * __ldcg(y + (size_t)__ldg(a.Lci + t) * k + c);
+                for (; t < dg; t += S) acc += lf[t] * __ldcg(y + (size_t)__ldg(a.Lci + t) * k + c);
             acc = slice_sum<LPR>(acc, kt, gmask);
-            if (s == 0 && c < k) y[(size_t)row * k + c] = (__ldg(b + (size_t)row * k + c) - acc) / lii;
+            if (s == 0 && c < k) y[(size_t)row * k + c] = ((c0 == 0 ? bv : __ldg(b + (size_t)row * k + c)) - acc) * ri;
         }
     }
     publish(a, row, epoch, gl, gmask, ok);
@@ -507,10 +616,12 @@ constexpr int kExecThreads = 256;
 
 // Resident blocks per SM the compiler budgets registers for: the default kernels keep all the
 // registers they want (latency-bound chains prefer fewer, faster threads); the occupancy
-// variants of value-flag kernels with up to four lanes per row are held to three blocks of
-// 256 threads (85 registers), for schedules bound by the number of rows in flight.
+// variants are held to three blocks of 256 threads (85 registers: value-flag kernels with up
+// to four lanes per row) or four (64 registers: IC0 kernels with whole-warp rows, which fit
+// there without spilling), for schedules bound by the number of rows in flight.
 constexpr int kMinBlocksDefault = 1;
 constexpr int kMinBlocksHigh = 3;
+constexpr int kMinBlocksIc0 = 4;
 
 // Next ticket of a team (its first lane draws it; the caller broadcasts it when needed, so
 // the atomic's latency overlaps the current partition's work).
@@ -592,6 +703,13 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
 template <int MODE, bool VF, int TEAM>
 const void *kernel_for_team(int dtype, int lpr, int minb) {
     constexpr int D = kMinBlocksDefault;
+    if constexpr ((MODE == M_IC0_TRSV || MODE == M_IC0) && TEAM == 32) {
+        if (minb >= kMinBlocksHigh && lpr == 32) {
+            constexpr int H = kMinBlocksIc0;
+            return dtype == 0 ? (const void *)k_exec<MODE, double, 32, VF, 32, H>
+                              : (const void *)k_exec<MODE, float, 32, VF, 32, H>;
+        }
+    }
     if constexpr (VF && TEAM == 32) {
         if (minb >= kMinBlocksHigh) {
             constexpr int H = kMinBlocksHigh;

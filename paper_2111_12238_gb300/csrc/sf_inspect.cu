@@ -629,6 +629,82 @@ cudaError_t place_g2(int n, int depth, int mode, int *level, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Zero-fill IC0 (§2.1, up-looking form): entry (i, j), j < i, subtracts the sum of L_ik L_jk
+// over the columns k < j present in both rows i and j. Those columns follow from the pattern
+// alone, so the inspector lists them once: for every entry t = (i, j), the pairs (p, q) of
+// entry positions with column k in row i (p < t) and in row j (q before row j's diagonal),
+// in increasing k. One warp per row, lanes over the row's off-diagonal entries, each a merge
+// of two sorted column lists.
+template <bool FILL>
+__global__ void k_ic0_pairs(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                            long long *__restrict__ cnt, const long long *__restrict__ off, int2 *__restrict__ pairs) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int rs = rp[i], dg = rp[i + 1] - 1;
+        for (int t = rs + lane; t < dg; t += 32) {
+            const int j = ci[t];
+            int p = rs, q = rp[j];
+            const int qe = rp[j + 1] - 1;   // row j's diagonal is its last entry
+            long long c = 0, w = FILL ? off[t] : 0;
+            while (p < t && q < qe) {
+                const int cp = ci[p], cq = ci[q];
+                if (cp == cq) {
+                    if (FILL) pairs[w++] = make_int2(p, q);
+                    else ++c;
+                    ++p;
+                    ++q;
+                } else if (cp < cq) {
+                    ++p;
+                } else {
+                    ++q;
+                }
+            }
+            if (!FILL) cnt[t] = c;
+        }
+        if (!FILL && lane == 0) cnt[dg] = 0;
+    }
+}
+
+__global__ void k_narrow_offsets(long long m, const long long *__restrict__ in, int *__restrict__ out) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long long)gridDim.x * blockDim.x)
+        out[t] = (int)in[t];
+}
+
+cudaError_t build_ic0_pairs(const DevCsr &L, long long max_pairs, int **pp_out, int2 **pairs_out, long long *np_out,
+                            cudaStream_t s, Arena &ar, Arena &keep) {
+    *pp_out = nullptr;
+    *pairs_out = nullptr;
+    *np_out = 0;
+    const long long nnz = L.nnz;
+    if (L.n_rows <= 0 || nnz <= 0) return cudaSuccess;
+    long long *cnt = (long long *)ar.alloc(sizeof(long long) * (nnz + 1));
+    long long *off = (long long *)ar.alloc(sizeof(long long) * (nnz + 1));
+    if (!cnt || !off) return cudaErrorMemoryAllocation;
+    const unsigned g = grid_for((long long)L.n_rows * 32, 256, 8192);
+    k_ic0_pairs<false><<<g, 256, 0, s>>>(L.n_rows, L.rowptr, L.colidx, cnt, nullptr, nullptr);
+    cudaError_t e = cudaMemsetAsync(cnt + nnz, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    e = scan_excl<long long>(cnt, off, nnz + 1, s, ar);
+    if (e != cudaSuccess) return e;
+    long long total = 0;
+    e = cudaMemcpyAsync(&total, off + nnz, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *np_out = total;
+    if (total > max_pairs || total > 0x7fffffffLL) return cudaSuccess;   // too many: searched per call instead
+    int *pp = (int *)keep.alloc(sizeof(int) * (nnz + 1));
+    int2 *pairs = (int2 *)keep.alloc(sizeof(int2) * std::max<long long>(total, 1));
+    if (!pp || !pairs) return cudaErrorMemoryAllocation;
+    k_narrow_offsets<<<grid_for(nnz + 1, 256, 4096), 256, 0, s>>>(nnz + 1, off, pp);
+    if (total > 0) k_ic0_pairs<true><<<g, 256, 0, s>>>(L.n_rows, L.rowptr, L.colidx, nullptr, off, pairs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *pp_out = pp;
+    *pairs_out = pairs;
+    return cudaStreamSynchronize(s);
+}
+
 // Partition classes of a separated schedule: class 1 when the partition's first vertex is a
 // second-kernel row (a sink of the joint DAG), else class 0. plist lists the class-0
 // partitions in increasing order, then the class-1 partitions in increasing order.

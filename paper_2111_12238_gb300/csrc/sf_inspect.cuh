@@ -74,6 +74,10 @@ cudaError_t prefix_costs(long long nv, int n1, const int *order, const int *cost
 cudaError_t cut_partitions(long long nv, const long long *S, const long long *cs, long long C, long long W,
                            int *part_ptr, unsigned char *part_wide, int *n_parts, cudaStream_t s, Arena &ar);
 cudaError_t place_g2(int n, int depth, int mode, int *level, cudaStream_t s);
+// IC0 intersection pairs (per L entry: the (p, q) positions of its common columns); nothing is
+// built (*pp_out NULL) when the total exceeds max_pairs.
+cudaError_t build_ic0_pairs(const DevCsr &L, long long max_pairs, int **pp_out, int2 **pairs_out, long long *np_out,
+                            cudaStream_t s, Arena &ar, Arena &keep);
 cudaError_t split_partition_classes(int P, const int *part_ptr, const int *order, int *plist, int *n_class0,
                                     cudaStream_t s, Arena &ar);
 cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, const int *level, const DevCsr *M,

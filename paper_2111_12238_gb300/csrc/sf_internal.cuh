@@ -82,6 +82,11 @@ struct ExecArgs {
     void *pack_vals;                    // their values (gathered every call)
     void *pack_aux;                     // (c_i, 1 / L_ii) per position (gathered every call)
     int pack_stride;
+    // IC0: per L entry t, pairs [ic0_pp[t], ic0_pp[t + 1]) of ic0_pairs are the (p, q) entry
+    // positions of the columns that rows i and j share below j (NULL: searched per call)
+    const int *ic0_pp;
+    const int2 *ic0_pairs;
+    void *ic0_rinv;                     // IC0: 1 / L_ii per row, written with the factor row
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)

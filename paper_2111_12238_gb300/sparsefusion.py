@@ -60,7 +60,8 @@ class SfInfo(C.Structure):
                 ("parts_class0", C.c_int32), ("adj_parts_class0", C.c_int32),
                 ("split_pct", C.c_int32), ("adj_split_pct", C.c_int32),
                 ("g2_placement", C.c_int32), ("adj_g2_placement", C.c_int32),
-                ("min_blocks", C.c_int32), ("adj_min_blocks", C.c_int32)]
+                ("min_blocks", C.c_int32), ("adj_min_blocks", C.c_int32),
+                ("ic0_pairs", C.c_int64), ("ic0_use_pairs", C.c_int32), ("reserved3", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -94,6 +95,7 @@ _SIGS = {
     "sf_schedule_set_split": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_replace": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "sf_schedule_set_occupancy": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_set_ic0_pairs": (C.c_int, [_P, C.c_int32]),
     "sf_schedule_set_exec_events": (C.c_int, [_P, C.c_int32, _P, _P]),
     "sf_schedule_launches": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
@@ -329,6 +331,11 @@ class Schedule:
         schedules bound by rows in flight)."""
         _check(load_library().sf_schedule_set_occupancy(self.handle, int(which), int(min_blocks)),
                "sf_schedule_set_occupancy")
+
+    def set_ic0_pairs(self, use: bool):
+        """IC0 schedules: read the inspector's intersection pairs (True) or search the common
+        columns on every call (False)."""
+        _check(load_library().sf_schedule_set_ic0_pairs(self.handle, int(bool(use))), "sf_schedule_set_ic0_pairs")
 
     def set_split(self, which=-1, class0_pct=0):
         """Runs the partitions that open with a first-kernel row on class0_pct percent of the

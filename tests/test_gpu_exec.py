@@ -78,6 +78,85 @@ def test_ic0_with_intersections_and_alone():
         assert vec_rel_err(host(lf), lf_ref) < 1e-12
 
 
+def _ic0_pair_count(L):
+    """Brute force over the pattern: sum over entries (i, j), j < i, of the columns k < j in
+    both row i and row j."""
+    rp, ci = np.asarray(L.rowptr), np.asarray(L.colidx)
+    rows = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(L.n_rows)]
+    total = 0
+    for i in range(L.n_rows):
+        for j in ci[rp[i]:rp[i + 1] - 1].tolist():
+            total += sum(1 for c in rows[i] & rows[j] if c < j)
+    return total
+
+
+def _ic0_dense_rows(n, density, seed):
+    """Lower part of a symmetric M-matrix with rows longer than a warp: off-diagonals
+    -|U[-1,1]|, diagonal 1 + the absolute row sum of the symmetric matrix."""
+    D = random_lower(n, density, seed)
+    off = -np.abs(np.tril(D, -1))
+    diag = 1.0 + np.abs(off + off.T).sum(axis=1)
+    return dense_to_csr(off + np.diag(diag))
+
+
+@pytest.mark.parametrize("case", ["stencil9", "long_rows"])
+@pytest.mark.parametrize("use_pairs", [True, False])
+def test_ic0_pairs_and_search_paths(case, use_pairs):
+    need_cuda()
+    if case == "stencil9":
+        nx = 30
+        offs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        n, rowptr, cols, soffs, Msk = I._stencil_pattern((nx, nx), offs)
+        vals = np.where(np.asarray([o == (0, 0) for o in soffs])[None, :], 9.0, -1.0)
+        L = I.lower_part(I._finish(n, n, rowptr, cols, np.broadcast_to(vals, Msk.shape)[Msk]))
+    else:
+        L = _ic0_dense_rows(300, 0.25, 41)
+    n = L.n_rows
+    lf_ref = oracle.ic0(L)
+    b = I.dense_vectors(n, 8, 5, 1)
+    lf_ref2, y_ref = oracle.ic0_trsv(L, b)
+    for lpr, kt in ((1, 0), (4, 0), (32, 0), (32, 4)):
+        sch = sf.inspect("ic0", dev_csr(L), lanes_per_row=lpr)
+        assert sch.info()["ic0_pairs"] == _ic0_pair_count(L)
+        sch.set_ic0_pairs(use_pairs)
+        assert sch.info()["ic0_use_pairs"] == int(use_pairs)
+        lf = torch.empty(L.nnz, device="cuda", dtype=torch.float64)
+        sch.execute(t(L.vals), x_save=lf)
+        sch.check()
+        assert vec_rel_err(host(lf), lf_ref) < 1e-12
+        st = sf.inspect("ic0_trsv", dev_csr(L), lanes_per_row=lpr, rhs_tile=kt)
+        st.set_ic0_pairs(use_pairs)
+        lf2 = torch.empty(L.nnz, device="cuda", dtype=torch.float64)
+        y = st.execute(t(L.vals), b=t(b), x_save=lf2)
+        st.check()
+        assert vec_rel_err(host(lf2), lf_ref2) < 1e-12
+        assert col_rel_err(host(y), y_ref) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_ic0_occupancy_variant(dtype):
+    need_cuda()
+    w = I.ic0_trsv_aniso3d(14, k=32)
+    lf_ref, y_ref = oracle.ic0_trsv(w.L, w.b)
+    sch = sf.inspect("ic0_trsv", dev_csr(w.L), lanes_per_row=32, rhs_tile=32)
+    sch.set_occupancy(0, 3)
+    assert sch.info()["min_blocks"] == 3
+    lf = torch.empty(w.L.nnz, device="cuda", dtype=dtype)
+    y = sch.execute(t(w.L.vals, dtype), b=t(w.b, dtype), x_save=lf)
+    sch.check()
+    assert vec_rel_err(host(lf), lf_ref) < TOL[dtype]
+    assert col_rel_err(host(y), y_ref) < TOL[dtype] * (10 if dtype == torch.float32 else 1)
+
+
+def test_ic0_pairs_setter_rejects_other_pairs():
+    need_cuda()
+    w = _lap3d(6, 1)
+    sch = sf.inspect("trsv", dev_csr(w.L))
+    assert sch.info()["ic0_pairs"] == 0
+    with pytest.raises(sf.SparseFusionError):
+        sch.set_ic0_pairs(True)
+
+
 @pytest.mark.parametrize("k,ef", [(1, False), (1, True), (5, False)])
 def test_trsv_alone_and_unfused_path(k, ef):
     need_cuda()

@@ -536,9 +536,13 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     a.ic0_rinv = S->ic0_rinv;
     const int dtype = dt == SF_F64 ? 0 : 1;
     void *vbuf = value_flag_buffer(mode, a);
-    const bool vf = k == 1 && !S->epoch_flags && vbuf != nullptr;
+    const bool ic0 = mode == M_IC0_TRSV || mode == M_IC0;
+    // IC0 rows publish through their values when the pair lists exist (any k; the flat
+    // index row * k + column of y must fit in an int)
+    const bool vf = ic0 ? (!S->epoch_flags && a.ic0_pp != nullptr && (long long)S->n * k <= 0x7fffffffLL)
+                        : (k == 1 && !S->epoch_flags && vbuf != nullptr);
     // row-block executor with packed records and bulk copies
-    if (vf && d.exec_mode == 4 && d.nb > 0) {
+    if (vf && !ic0 && d.exec_mode == 4 && d.nb > 0) {
         const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
         const int rows = std::min(d.B, S->n);
         const int occ = block_tma_fits(mode, dtype, rows, nc);
@@ -565,7 +569,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         return SF_OK;
     }
     // warp-specialised row-block executor
-    if (vf && d.exec_mode == 3 && d.nb > 0) {
+    if (vf && !ic0 && d.exec_mode == 3 && d.nb > 0) {
         // consumer threads: one per position of the widest segment, a power of two in [32, 256]
         const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
         const int rows = std::min(d.B, S->n);
@@ -588,7 +592,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     }
     // the row-block executor serves one right-hand side with value flags (its pre-pass
     // resets the published vector)
-    if (vf && d.exec_mode == 2 && d.nb > 0) {
+    if (vf && !ic0 && d.exec_mode == 2 && d.nb > 0) {
         const int threads = block_threads(d);
         const int occ = block_exec_occupancy(mode, dtype, d.blpr, std::min(d.B, S->n), threads);
         if (occ > 0) {
@@ -611,7 +615,13 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         }
         return fail(SF_ERR_UNSUPPORTED, "row blocks of %d rows do not fit in shared memory", d.B);
     }
-    if (vf) {
+    if (vf && ic0) {
+        // value-flag reset (all bits set): y, 1 / L_ii, and the factor when pairs read it
+        const size_t es = dt == SF_F64 ? 8 : 4;
+        if (a.y) SF_CK(cudaMemsetAsync(a.y, 0xff, es * (size_t)S->n * (size_t)k, s), "value-flag reset");
+        SF_CK(cudaMemsetAsync(a.ic0_rinv, 0xff, es * (size_t)S->n, s), "value-flag reset");
+        if (S->ic0_npairs > 0) SF_CK(cudaMemsetAsync(a.xs, 0xff, es * (size_t)S->L.nnz, s), "value-flag reset");
+    } else if (vf) {
         // value-flag reset and reciprocal diagonals in one pass
         a.rdiag = d.aux;
         SF_CK(launch_rdiag(dtype, S->n, S->L.rowptr, a.Lv, vbuf, d.aux, d.st, s), "value-flag reset");

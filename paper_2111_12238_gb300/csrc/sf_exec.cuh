@@ -166,6 +166,23 @@ __device__ __forceinline__ bool wait_values(const T *vec, const int (&j)[U], T (
     return true;
 }
 
+// One value-flag load: p[0] once it is no longer the reset pattern (ok false on a timeout).
+template <typename T>
+__device__ __forceinline__ T poll_value(const T *p, ExecState *st, unsigned long long tmo, int row, bool &ok) {
+    T v = ld_relaxed_val(p);
+    if (!is_unset(v)) return v;
+    Waiter w;
+    while (ok) {
+        if (!w.pause(st, tmo, row)) {
+            ok = false;
+            break;
+        }
+        v = ld_relaxed_val(p);
+        if (!is_unset(v)) break;
+    }
+    return v;
+}
+
 // Dependency mode of a row dot product.
 enum Dep { D_NONE = 0, D_FLAG = 1, D_VALUE = 2 };
 
@@ -375,9 +392,9 @@ __device__ __forceinline__ T ic0_row_search(const ExecArgs &a, int rs, int dg, i
 // table the rows publish with their factor (a.ic0_rinv), so an entry costs one multiply. The
 // first chunk's pattern and A values (j0, q0, q1, av0) were loaded before the wait. Returns
 // sum_{k<i} L_ik^2 on every lane; the sum runs over the lanes that hold entries only.
-template <typename T, int LPR>
-__device__ __forceinline__ T ic0_row_pairs(const ExecArgs &a, int rs, int dg, int gl, unsigned gmask, int j0, int q0,
-                                           int q1, T av0) {
+template <typename T, int LPR, bool VF>
+__device__ __forceinline__ T ic0_row_pairs(const ExecArgs &a, int row, int rs, int dg, int gl, unsigned gmask, int j0,
+                                           int q0, int q1, T av0, bool &ok) {
     const T *Av = (const T *)a.Lv;
     const T *rinv = (const T *)a.ic0_rinv;
     T *lf = (T *)a.xs;
@@ -394,11 +411,12 @@ __device__ __forceinline__ T ic0_row_pairs(const ExecArgs &a, int rs, int dg, in
             p1 = __ldg(a.ic0_pp + t + 1);
             av = __ldg(Av + t);
         }
-        const T rj = mine ? __ldcg(rinv + j) : T(0);
+        T rj = T(0);
+        if (mine) rj = VF ? poll_value(rinv + j, a.st, a.timeout_ns, row, ok) : __ldcg(rinv + j);
         T v = T(0);
         if (mine && p0 == p1) {
             v = av * rj;
-            lf[t] = v;
+            store_out<VF>(lf + t, v);
         }
         unsigned serial = __ballot_sync(gmask, mine && p0 < p1);
         if (serial) {
@@ -410,12 +428,13 @@ __device__ __forceinline__ T ic0_row_pairs(const ExecArgs &a, int rs, int dg, in
                 T part = T(0);
                 for (int g = s0 + gl; g < s1; g += LPR) {
                     const int2 pq = __ldg(a.ic0_pairs + g);
-                    part += lf[pq.x] * __ldcg(lf + pq.y);
+                    const T lq = VF ? poll_value(lf + pq.y, a.st, a.timeout_ns, row, ok) : __ldcg(lf + pq.y);
+                    part += lf[pq.x] * lq;
                 }
                 part = group_sum<LPR>(part, gmask);
                 if (gl == src - gbase) {
                     v = (av - part) * rj;
-                    lf[t] = v;
+                    store_out<VF>(lf + t, v);
                 }
                 __syncwarp(gmask);
             }
@@ -437,7 +456,10 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 // / L_jj; then L_ii = sqrt(A_ii - sum_{k<i} L_ik^2); then the solve row with the fresh
 // L_i on chip: y_i = (b_i - sum_j L_ij y_j) / L_ii. Factor values go to a.xs; 1 / L_ii goes
 // to a.ic0_rinv with them (one reciprocal square root gives both L_ii and 1 / L_ii).
-template <typename T, int LPR, bool SOLVE>
+// With value flags (VF; the pair lists are then present) nothing waits on epoch flags: the
+// factor polls 1 / L_jj and the factor entries its pairs read, each solve lane polls its
+// column of the predecessor rows of y, and every such value is stored as its own flag.
+template <typename T, int LPR, bool SOLVE, bool VF>
 __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
     const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Av = (const T *)a.Lv;
@@ -454,7 +476,7 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
     const T aii = __ldg(Av + dg);
     bool ok = true;
     // every predecessor row publishes its factor row and its solve row together
-    for (int e = rs + gl; e < dg; e += LPR * kUnroll) {
+    for (int e = rs + gl; !VF && e < dg; e += LPR * kUnroll) {
         int j[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
@@ -472,21 +494,32 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
     if (SOLVE) {
         const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
         const T *y = (const T *)a.y;
+        if constexpr (VF) {
+            int jy[kY];
 #pragma unroll
-        for (int u = 0; u < kY; ++u) {
-            const int t = rs + s + u * S;
-            yv[u] = (cl < k && t < dg) ? __ldcg(y + (size_t)__ldg(a.Lci + t) * k + cl) : T(0);
+            for (int u = 0; u < kY; ++u) {
+                const int t = rs + s + u * S;
+                jy[u] = (cl < k && t < dg) ? __ldg(a.Lci + t) * k + cl : -1;
+            }
+            if (!wait_values<T, kY>(y, jy, yv, a.st, a.timeout_ns, row)) ok = false;
+        } else {
+#pragma unroll
+            for (int u = 0; u < kY; ++u) {
+                const int t = rs + s + u * S;
+                yv[u] = (cl < k && t < dg) ? __ldcg(y + (size_t)__ldg(a.Lci + t) * k + cl) : T(0);
+            }
         }
         if (s == 0 && cl < k) bv = __ldg((const T *)a.b + (size_t)row * k + cl);
     }
-    const T sq = a.ic0_pp ? ic0_row_pairs<T, LPR>(a, rs, dg, gl, gmask, j0, q0, q1, av0)
-                          : ic0_row_search<T, LPR>(a, rs, dg, gl, gmask);
+    T sq;
+    if (VF || a.ic0_pp) sq = ic0_row_pairs<T, LPR, VF>(a, row, rs, dg, gl, gmask, j0, q0, q1, av0, ok);
+    else sq = ic0_row_search<T, LPR>(a, rs, dg, gl, gmask);
     const T dd = aii - sq;
     if (gl == 0 && !(dd > T(0))) record_error(a.st, SF_ERR_BREAKDOWN, row);
     const T ri = rsqrt_t(dd);
     if (gl == 0) {
         lf[dg] = dd * ri;
-        ((T *)a.ic0_rinv)[row] = ri;
+        store_out<VF>((T *)a.ic0_rinv + row, ri);
     }
     if (SOLVE) {
         const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
@@ -504,11 +537,16 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
                 t += kY * S;
             }
             if (c < k)
-                for (; t < dg; t += S) acc += lf[t] * __ldcg(y + (size_t)__ldg(a.Lci + t) * k + c);
+                for (; t < dg; t += S) {
+                    const T *yp = y + (size_t)__ldg(a.Lci + t) * k + c;
+                    acc += lf[t] * (VF ? poll_value(yp, a.st, a.timeout_ns, row, ok) : __ldcg(yp));
+                }
             acc = slice_sum<LPR>(acc, kt, gmask);
-            if (s == 0 && c < k) y[(size_t)row * k + c] = ((c0 == 0 ? bv : __ldg(b + (size_t)row * k + c)) - acc) * ri;
+            if (s == 0 && c < k)
+                store_out<VF>(y + (size_t)row * k + c, ((c0 == 0 ? bv : __ldg(b + (size_t)row * k + c)) - acc) * ri);
         }
     }
+    if (VF) return group_ok<LPR>(ok, gmask);
     publish(a, row, epoch, gl, gmask, ok);
     return ok;
 }
@@ -584,9 +622,10 @@ __device__ bool item_adj_gx(const ExecArgs &a, int j, unsigned epoch, int gl, un
     return group_ok<LPR>(ok, gmask);
 }
 
-// Modes whose k = 1 launches use value flags.
+// Modes with value-flag launches (k = 1; IC0 modes for any k when the pair lists exist).
 constexpr bool mode_has_vf(int m) {
-    return m == M_TRSV_SPMV || m == M_TRSV || m == M_SPMV_TRSV || m == M_ADJ_TRSV_SPMV || m == M_ADJ_SPMV_TRSV;
+    return m == M_TRSV_SPMV || m == M_TRSV || m == M_SPMV_TRSV || m == M_ADJ_TRSV_SPMV || m == M_ADJ_SPMV_TRSV ||
+           m == M_IC0_TRSV || m == M_IC0;
 }
 
 template <int MODE, typename T, int LPR, bool VF>
@@ -600,9 +639,9 @@ __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, un
     } else if constexpr (MODE == M_SPMV_TRSV) {
         return item_spmv_trsv<T, LPR, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0_TRSV) {
-        return item_ic0<T, LPR, true>(a, row, epoch, gl, gmask);
+        return item_ic0<T, LPR, true, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0) {
-        return item_ic0<T, LPR, false>(a, row, epoch, gl, gmask);
+        return item_ic0<T, LPR, false, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_ADJ_TRSV_SPMV) {
         return item_adj_trsv_spmv<T, LPR, VF>(a, row, epoch, gl, gbase, gmask);
     } else {

@@ -123,6 +123,12 @@ cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void 
                          cudaStream_t s);
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team, int minb);
+cudaError_t launch_exec_ic0(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
+                            const ExecArgs &a);
+int occupancy_ic0(int mode, int dtype, int lpr, bool vf, int team, int minb);
+cudaError_t launch_exec_ic0_alone(int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
+                                  const ExecArgs &a);
+int occupancy_ic0_alone(int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team, int minb);
 // Adjoint helpers: dst[t] = src[perm[t]] (values in transposed order), and the value
 // gradients out[e] = sign * sum_c coef[i*k+c] * vec[col(e)*k+c] over the rows i of a pattern.

@@ -91,6 +91,34 @@ def test_timeout_is_reported_not_hung(ef):
     assert col_rel_err(host(x), oracle.trsv_lower(L, b)) < 1e-14
 
 
+@pytest.mark.parametrize("pair,k", [("ic0_trsv", 4), ("ic0", 1)])
+def test_ic0_value_flag_timeout_is_reported(pair, k):
+    # IC0 rows poll 1 / L_jj and their columns of y (value flags). A chain in one partition
+    # with its first two items swapped makes row 1 poll values that only row 0, later in the
+    # same team's list, would write; the bounded poll must end with SF_ERR_TIMEOUT.
+    need_cuda()
+    n = 48
+    D = np.eye(n) * 4 - np.eye(n, k=-1)
+    L = dense_to_csr(D)
+    b = I.dense_vectors(n, k, 9, 1)
+    sch = sf.inspect(pair, dev_csr(L), lanes_per_row=32, part_cost_target=10 ** 9)
+    assert sch.info()["n_parts"] == 1 and sch.info()["ic0_use_pairs"] == 1
+    sch.set_timeout(2_000_000)
+    sch.debug_swap(0, 1)
+    lf = torch.empty(L.nnz, device="cuda", dtype=torch.float64)
+    Lv, bb = t(L.vals), t(b)
+    run = (lambda: sch.execute(Lv, b=bb, x_save=lf)) if pair == "ic0_trsv" else (lambda: sch.execute(Lv, x_save=lf))
+    run()
+    st, row = sch.check_status()
+    assert (st, row) == (5, 1)          # SF_ERR_TIMEOUT at row 1
+    sch.debug_swap(0, 1)
+    y = run()
+    sch.check()
+    assert vec_rel_err(host(lf), oracle.ic0(L)) < 1e-14
+    if pair == "ic0_trsv":
+        assert col_rel_err(host(y), oracle.ic0_trsv(L, b)[1]) < 1e-13
+
+
 def test_ic0_breakdown_and_zero_pivot_reported():
     need_cuda()
     D = np.array([[1.0, 0, 0], [2.0, 1.0, 0], [0, 0, 1.0]])

@@ -100,8 +100,10 @@ def _ic0_dense_rows(n, density, seed):
 
 
 @pytest.mark.parametrize("case", ["stencil9", "long_rows"])
-@pytest.mark.parametrize("use_pairs", [True, False])
-def test_ic0_pairs_and_search_paths(case, use_pairs):
+@pytest.mark.parametrize("path", ["value_flags", "epoch_flags", "search"])
+def test_ic0_pairs_and_search_paths(case, path):
+    # value_flags: pair lists, every value its own ready flag (the default); epoch_flags: pair
+    # lists with per-row flags; search: common columns searched per call (per-row flags)
     need_cuda()
     if case == "stencil9":
         nx = 30
@@ -116,7 +118,9 @@ def test_ic0_pairs_and_search_paths(case, use_pairs):
     b = I.dense_vectors(n, 8, 5, 1)
     lf_ref2, y_ref = oracle.ic0_trsv(L, b)
     for lpr, kt in ((1, 0), (4, 0), (32, 0), (32, 4)):
-        sch = sf.inspect("ic0", dev_csr(L), lanes_per_row=lpr)
+        use_pairs = path != "search"
+        ef = path == "epoch_flags"
+        sch = sf.inspect("ic0", dev_csr(L), lanes_per_row=lpr, epoch_flags=ef)
         assert sch.info()["ic0_pairs"] == _ic0_pair_count(L)
         sch.set_ic0_pairs(use_pairs)
         assert sch.info()["ic0_use_pairs"] == int(use_pairs)
@@ -124,7 +128,7 @@ def test_ic0_pairs_and_search_paths(case, use_pairs):
         sch.execute(t(L.vals), x_save=lf)
         sch.check()
         assert vec_rel_err(host(lf), lf_ref) < 1e-12
-        st = sf.inspect("ic0_trsv", dev_csr(L), lanes_per_row=lpr, rhs_tile=kt)
+        st = sf.inspect("ic0_trsv", dev_csr(L), lanes_per_row=lpr, rhs_tile=kt, epoch_flags=ef)
         st.set_ic0_pairs(use_pairs)
         lf2 = torch.empty(L.nnz, device="cuda", dtype=torch.float64)
         y = st.execute(t(L.vals), b=t(b), x_save=lf2)

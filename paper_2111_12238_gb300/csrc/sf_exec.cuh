@@ -186,6 +186,108 @@ __device__ __forceinline__ T poll_value(const T *p, ExecState *st, unsigned long
 // Dependency mode of a row dot product.
 enum Dep { D_NONE = 0, D_FLAG = 1, D_VALUE = 2 };
 
+// Epoch-flag read for the scans below: relaxed, and free to overlap with the loads around it
+// (the acquire fence that follows a scan orders the data loads).
+__device__ __forceinline__ unsigned ld_flag_scan(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Entries of a row whose epoch flag was unset at the scan; flags read per lane per scan round;
+// data loads in flight per lane.
+constexpr int kPend = 8;
+constexpr int kScanU = 16;
+constexpr int kDataU = 8;
+
+// row_dot with epoch flags, as a sliding window over the lane's slice of the row: a scan reads
+// the flags ahead without fences and notes the first kPend entries whose rows are unpublished,
+// stopping at the next one; one acquire fence; the published entries before that point stream
+// with kDataU loads in flight; then the noted entries wait together (one fence) and load
+// together, and the window moves on. A long row does most of its work before its last input
+// arrives, with no fence between the loads of published entries.
+template <typename T, bool PERM>
+__device__ __forceinline__ T row_dot_flags(const int *__restrict__ cols, const int *__restrict__ perm,
+                                           const T *__restrict__ vals, int e0, int e1, int S, const T *vec, int k,
+                                           int c, bool act, const unsigned *flags, unsigned epoch, ExecState *st,
+                                           unsigned long long tmo, int row, bool &ok) {
+    T acc = T(0);
+    int e = e0;
+    while (e < e1 && ok) {
+        int pend[kPend];
+#pragma unroll
+        for (int q = 0; q < kPend; ++q) pend[q] = -1;
+        int np = 0, stop = e1;
+        for (int f = e; f < e1 && stop == e1; f += S * kScanU) {
+            int j[kScanU];
+            unsigned fl[kScanU];
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) {
+                const int ee = f + u * S;
+                j[u] = ee < e1 ? __ldg(cols + ee) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u) fl[u] = j[u] >= 0 ? ld_flag_scan(flags + j[u]) : epoch;
+#pragma unroll
+            for (int u = 0; u < kScanU; ++u)
+                if (fl[u] != epoch && stop == e1) {
+                    const int ee = f + u * S;
+                    if (np < kPend) {
+#pragma unroll
+                        for (int q = 0; q < kPend; ++q)
+                            if (q == np) pend[q] = ee;
+                        ++np;
+                    } else {
+                        stop = ee;
+                    }
+                }
+        }
+        fence_acq_rel_gpu();
+        if (act) {
+            for (int f = e; f < stop; f += S * kDataU) {
+                T vv[kDataU], xv[kDataU];
+#pragma unroll
+                for (int u = 0; u < kDataU; ++u) {
+                    const int ee = f + u * S;
+                    bool use = ee < stop;
+#pragma unroll
+                    for (int q = 0; q < kPend; ++q) use &= pend[q] != ee;
+                    vv[u] = T(0);
+                    xv[u] = T(0);
+                    if (use) {
+                        vv[u] = __ldg(vals + (PERM ? __ldg(perm + ee) : ee));
+                        xv[u] = __ldcg(vec + (size_t)__ldg(cols + ee) * k + c);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kDataU; ++u) acc += vv[u] * xv[u];
+            }
+        }
+        if (np > 0) {
+            int jp[kPend];
+#pragma unroll
+            for (int q = 0; q < kPend; ++q) jp[q] = pend[q] >= 0 ? __ldg(cols + pend[q]) : -1;
+            ok = wait_flags<kPend>(flags, jp, epoch, st, tmo, row);
+            if (act && ok) {
+                T vv[kPend], xv[kPend];
+#pragma unroll
+                for (int q = 0; q < kPend; ++q) {
+                    vv[q] = T(0);
+                    xv[q] = T(0);
+                    if (jp[q] >= 0) {
+                        vv[q] = __ldg(vals + (PERM ? __ldg(perm + pend[q]) : pend[q]));
+                        xv[q] = __ldcg(vec + (size_t)jp[q] * k + c);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kPend; ++q) acc += vv[q] * xv[q];
+            }
+        }
+        e = stop;
+    }
+    return acc;
+}
+
 // acc = sum over this lane's slice of entries e in [e0, e1) (stride S) of
 // vals[PERM ? perm[e] : e] * vec[cols[e] * k + c]. D_FLAG / D_VALUE wait for the rows
 // cols[e] first (vec is produced by other warps in this launch).
@@ -194,6 +296,30 @@ __device__ __forceinline__ T row_dot(const int *__restrict__ cols, const int *__
                                      const T *__restrict__ vals, int e0, int e1, int S, const T *vec,
                                      int k, int c, bool act, const unsigned *flags, unsigned epoch,
                                      ExecState *st, unsigned long long tmo, int row, bool &ok) {
+    if constexpr (DEP == D_FLAG)
+        return row_dot_flags<T, PERM>(cols, perm, vals, e0, e1, S, vec, k, c, act, flags, epoch, st, tmo, row, ok);
+    if constexpr (DEP == D_NONE) {
+        // nothing to wait for: kDataU loads in flight per lane, issued before their products
+        T acc = T(0);
+        if (act) {
+            for (int e = e0; e < e1; e += S * kDataU) {
+                T vv[kDataU], xv[kDataU];
+#pragma unroll
+                for (int u = 0; u < kDataU; ++u) {
+                    const int ee = e + u * S;
+                    vv[u] = T(0);
+                    xv[u] = T(0);
+                    if (ee < e1) {
+                        vv[u] = __ldg(vals + (PERM ? __ldg(perm + ee) : ee));
+                        xv[u] = __ldg(vec + (size_t)__ldg(cols + ee) * k + c);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kDataU; ++u) acc += vv[u] * xv[u];
+            }
+        }
+        return acc;
+    }
     T acc = T(0);
     for (int e = e0; e < e1; e += S * kUnroll) {
         int j[kUnroll];

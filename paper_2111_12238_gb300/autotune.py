@@ -155,11 +155,19 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
         if best is None or ms < best["ms"]:
             best = trials[-1]
     separated = inf["parts_class0" if which == 0 else "adj_parts_class0"] > 0
-    # separated schedules: the best shape with the second kernel's vertices placed later
-    # (slack, section 3.2.2), then with the teams split between the two partition classes
+    # separated schedules: the best shape, and the best row-block shape, with the second
+    # kernel's vertices placed later (slack, section 3.2.2); then the best partition shape
+    # with the teams split between the two partition classes
     if best is not None and separated and placements:
-        for g2 in placements:
-            c = {kk: v for kk, v in best.items() if kk not in ("ms", "part_cost_target", "cached")}
+        bases = [best]
+        rb = [t for t in trials if t["exec"] in ("ws", "tma", "blocks")]
+        if rb:
+            rb_best = min(rb, key=lambda t: t["ms"])
+            if rb_best is not best:
+                bases.append(rb_best)
+        shapes = [(b, g2) for b in bases for g2 in placements]
+        for base, g2 in shapes:
+            c = {kk: v for kk, v in base.items() if kk not in ("ms", "part_cost_target", "cached")}
             c["g2"] = g2
             try:
                 _apply(sched, which, c, mean)

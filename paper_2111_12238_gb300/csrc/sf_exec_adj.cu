@@ -1,5 +1,6 @@
-// Executor instantiations: the two adjoint passes, plus the adjoint's two streaming helpers
-// (values in transposed order, and the pattern-restricted value gradients).
+// Executor instantiations: the adjoint pass of SpTRSV -> SpMV (that of SpMV -> SpTRSV is in
+// sf_exec_adj2.cu), plus the adjoint's two streaming helpers (values in transposed order,
+// and the pattern-restricted value gradients).
 #include "sf_exec.cuh"
 
 namespace sf {
@@ -7,13 +8,13 @@ namespace sf {
 cudaError_t launch_exec_adj(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                             const ExecArgs &a) {
     if (mode == M_ADJ_TRSV_SPMV) return launch_mode<M_ADJ_TRSV_SPMV>(dtype, lpr, vf, team, minb, blocks, s, a);
-    if (mode == M_ADJ_SPMV_TRSV) return launch_mode<M_ADJ_SPMV_TRSV>(dtype, lpr, vf, team, minb, blocks, s, a);
+    if (mode == M_ADJ_SPMV_TRSV) return launch_exec_adj2(dtype, lpr, vf, team, minb, blocks, s, a);
     return cudaErrorInvalidValue;
 }
 
 int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team, int minb) {
     if (mode == M_ADJ_TRSV_SPMV) return blocks_per_sm_mode<M_ADJ_TRSV_SPMV>(dtype, lpr, vf, team, minb);
-    return blocks_per_sm_mode<M_ADJ_SPMV_TRSV>(dtype, lpr, vf, team, minb);
+    return occupancy_adj2(dtype, lpr, vf, team, minb);
 }
 
 template <typename T>

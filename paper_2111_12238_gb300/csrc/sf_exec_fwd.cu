@@ -1,5 +1,5 @@
-// Executor instantiations: SpTRSV -> SpMV (separated items) and SpTRSV alone, plus the
-// plain SpMV kernel of the unfused two-launch path.
+// Executor instantiations: SpTRSV -> SpMV (separated items; SpTRSV alone is in
+// sf_exec_trsv.cu), plus the plain SpMV kernel of the unfused two-launch path.
 #include "sf_exec.cuh"
 
 namespace sf {
@@ -7,13 +7,13 @@ namespace sf {
 cudaError_t launch_exec_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                             const ExecArgs &a) {
     if (mode == M_TRSV_SPMV) return launch_mode<M_TRSV_SPMV>(dtype, lpr, vf, team, minb, blocks, s, a);
-    if (mode == M_TRSV) return launch_mode<M_TRSV>(dtype, lpr, vf, team, minb, blocks, s, a);
+    if (mode == M_TRSV) return launch_exec_trsv(dtype, lpr, vf, team, minb, blocks, s, a);
     return cudaErrorInvalidValue;
 }
 
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb) {
     if (mode == M_TRSV_SPMV) return blocks_per_sm_mode<M_TRSV_SPMV>(dtype, lpr, vf, team, minb);
-    return blocks_per_sm_mode<M_TRSV>(dtype, lpr, vf, team, minb);
+    return occupancy_trsv(dtype, lpr, vf, team, minb);
 }
 
 // y = M x or y = b - M x, one group of LPR lanes per row, rows in order (no

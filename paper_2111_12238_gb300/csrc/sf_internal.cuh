@@ -123,6 +123,12 @@ cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void 
                          cudaStream_t s);
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team, int minb);
+cudaError_t launch_exec_trsv(int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
+                             const ExecArgs &a);
+int occupancy_trsv(int dtype, int lpr, bool vf, int team, int minb);
+cudaError_t launch_exec_adj2(int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
+                             const ExecArgs &a);
+int occupancy_adj2(int dtype, int lpr, bool vf, int team, int minb);
 cudaError_t launch_exec_ic0(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                             const ExecArgs &a);
 int occupancy_ic0(int mode, int dtype, int lpr, bool vf, int team, int minb);

@@ -791,6 +791,7 @@ SF_API sf_status sf_execute(const sf_schedule *S, sf_dtype dt, int32_t k, const 
             break;
         case SF_IC0:
             if (!x_save) return fail(SF_ERR_INVALID_ARG, "SF_IC0 needs x_save (the factor values)");
+            if (M_vals || x_in || b || y) return fail(SF_ERR_INVALID_ARG, "M_vals, x_in, b and y must be NULL for SF_IC0");
             mode = M_IC0;
             break;
     }

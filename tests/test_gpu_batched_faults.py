@@ -137,6 +137,19 @@ def test_ic0_breakdown_and_zero_pivot_reported():
     assert st == 0                      # the report is cleared once read
 
 
+def test_ic0_alone_rejects_solve_operands():
+    need_cuda()
+    L = dense_to_csr(np.eye(4) * 4 - np.eye(4, k=-1))
+    sch = sf.inspect("ic0", dev_csr(L))
+    lf = torch.empty(L.nnz, device="cuda", dtype=torch.float64)
+    with pytest.raises(sf.SparseFusionError) as e:
+        sch.execute(t(L.vals), y=torch.empty((4, 1), device="cuda", dtype=torch.float64), x_save=lf)
+    assert e.value.status == 1
+    sch.execute(t(L.vals), x_save=lf)
+    sch.check()
+    assert vec_rel_err(host(lf), oracle.ic0(L)) < 1e-14
+
+
 def test_invalid_execute_arguments():
     need_cuda()
     w = I.trsv_spmv_lap2d(8, seed=1)

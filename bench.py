@@ -310,6 +310,24 @@ def t_hop_ns(torch, device):
     return ms / 3 * 1e6 / n
 
 
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(x, world, device):
+    """The largest of one float per rank, on every rank (torch.distributed, any backend);
+    x itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, slowest_ms):
+    """Whole-job throughput: every rank ran `steps` solves; the job took the slowest rank's
+    time."""
+    return world * steps / (slowest_ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- arms
 def run_gpu(args):
     import torch
@@ -386,12 +404,9 @@ def run_gpu(args):
         g.sched.set_exec_events(w, None, None)
     exec_ms = {w: sum(a_.elapsed_time(b_) for a_, b_ in kev[w]) / args.steps for w in dirs}
     g.check()
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, device)
     ms_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_value(world, args.steps, total_ms)
     fwd_ms = per[0] / args.steps
     adj_ms = per[1] / args.steps if wl["adj"] else None
 
@@ -426,10 +441,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         e2e_step()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, device)
     g.check()
     h2d = pin_b.numel() * pin_b.element_size() + (pin_gy.numel() * pin_gy.element_size() if pin_gy is not None else 0)
     d2h = out_y.numel() * out_y.element_size() + (out_gb.numel() * out_gb.element_size() if out_gb is not None else 0)
@@ -505,7 +517,7 @@ def run_gpu(args):
         "exec": {"fwd": info["exec_mode"], "adj": info["adj_exec_mode"], "block_rows": info["block_rows"],
                  "n_blocks": info["n_blocks"], "block_lanes": info["block_lanes"]},
         "tuned": tuned,
-        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(world, e2e_steps, e2e_s * 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         # our kernels per step, as the library counts them for the tuned launch shapes:
         # pre-passes, value gathers, fused kernels and gradient passes

@@ -61,7 +61,7 @@ def _load():
             for name in ("orc_trsv_lower", "orc_spmv", "orc_residual", "orc_ic0", "orc_trsv_lower_T",
                          "orc_spmv_T", "orc_trsv_spmv", "orc_spmv_trsv", "orc_ic0_trsv",
                          "orc_adj_trsv_spmv", "orc_adj_spmv_trsv", "orc_levels", "orc_costs",
-                         "orc_order", "orc_validate"):
+                         "orc_order", "orc_validate", "orc_trsv_trsv", "orc_ilu0", "orc_ilu0_trsv"):
                 getattr(lib, name).restype = C.c_int
             lib.orc_partition.restype = C.c_int64
             lib.orc_block_order.restype = C.c_int64
@@ -211,6 +211,40 @@ def ic0_trsv(L, b):
     _check(lib.orc_ic0_trsv(C.c_int32(L.n_rows), C.c_int32(b.shape[1]), rp, ci, v, pb, pl, py),
            "ic0_trsv")
     return lf, y
+
+
+def trsv_trsv(L, b):
+    """(x, z): x = L^-1 b, then z = L^-1 x (Table 2 combination 1)."""
+    lib = _load()
+    b = _block(b, L.n_rows)
+    keep, rp, ci, v = _csr(L)
+    bb, pb = _f64(b)
+    x, px = _out(b.shape)
+    z, pz = _out(b.shape)
+    _check(lib.orc_trsv_trsv(C.c_int32(L.n_rows), C.c_int32(b.shape[1]), rp, ci, v, pb, px, pz), "trsv_trsv")
+    return x, z
+
+
+def ilu0(A):
+    """Zero fill-in incomplete LU of A on A's pattern: the strictly lower part of the unit
+    lower factor and the upper factor with its diagonal (Table 2 combination 6)."""
+    lib = _load()
+    keep, rp, ci, v = _csr(A)
+    lu, pl = _out(A.nnz)
+    _check(lib.orc_ilu0(C.c_int32(A.n_rows), rp, ci, v, pl), "ilu0")
+    return lu
+
+
+def ilu0_trsv(A, b):
+    """(lu, y): ILU0 of A, then y = L^-1 b with its unit lower factor."""
+    lib = _load()
+    b = _block(b, A.n_rows)
+    keep, rp, ci, v = _csr(A)
+    bb, pb = _f64(b)
+    lu, pl = _out(A.nnz)
+    y, py = _out(b.shape)
+    _check(lib.orc_ilu0_trsv(C.c_int32(A.n_rows), C.c_int32(b.shape[1]), rp, ci, v, pb, pl, py), "ilu0_trsv")
+    return lu, y
 
 
 def adj_trsv_spmv(L, M, x, gy):

@@ -173,6 +173,65 @@ int orc_ic0_trsv(int32_t n, int32_t k, const int32_t *rp, const int32_t *ci, con
     return orc_trsv_lower(n, k, rp, ci, lfac, b, y);
 }
 
+/* Table 2 combination 1: x = L^-1 b, then z = L^-1 x with the same L (two forward
+ * substitutions in program order). */
+int orc_trsv_trsv(int32_t n, int32_t k, const int32_t *rp, const int32_t *ci, const double *v,
+                  const double *b, double *x, double *z) {
+    int st = orc_trsv_lower(n, k, rp, ci, v, b, x);
+    if (st) return st;
+    return orc_trsv_lower(n, k, rp, ci, v, x, z);
+}
+
+/* position of column j in row i (ascending columns), or -1 */
+static int64_t find_col(const int32_t *rp, const int32_t *ci, int32_t i, int32_t j) {
+    int64_t lo = rp[i], hi = rp[i + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (ci[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < rp[i + 1] && ci[lo] == j) ? lo : -1;
+}
+
+/* Zero fill-in incomplete LU of a square A with its diagonal present (Table 2 combination 6),
+ * in the row-oriented IKJ form (Saad, Iterative Methods for Sparse Linear Systems, Alg. 10.4):
+ * for each row i, for each k < i in the row, ascending: a_ik /= u_kk, then every later entry
+ * a_ij of row i with (k, j) in the pattern loses a_ik * u_kj. The result lu holds the strictly
+ * lower part of the unit lower factor L and the upper factor U (diagonal included) on A's
+ * pattern. Returns -(i+1) for a missing diagonal, +(k+1) for a zero pivot u_kk. */
+int orc_ilu0(int32_t n, const int32_t *rp, const int32_t *ci, const double *a, double *lu) {
+    memcpy(lu, a, sizeof(double) * (size_t)rp[n]);
+    for (int32_t i = 0; i < n; ++i)
+        if (diag_pos(rp, ci, i) < 0) return -(i + 1);
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t e = rp[i]; e < rp[i + 1] && ci[e] < i; ++e) {
+            int32_t kr = ci[e];
+            int64_t dk = diag_pos(rp, ci, kr);
+            if (lu[dk] == 0.0) return kr + 1;
+            lu[e] /= lu[dk];
+            for (int64_t f = e + 1; f < rp[i + 1]; ++f) {
+                int64_t g = find_col(rp, ci, kr, ci[f]);
+                if (g >= 0) lu[f] -= lu[e] * lu[g];
+            }
+        }
+    }
+    return OK;
+}
+
+/* ILU0, then y = L^-1 b with the unit lower factor L of lu (Table 2 combination 6). */
+int orc_ilu0_trsv(int32_t n, int32_t k, const int32_t *rp, const int32_t *ci, const double *a,
+                  const double *b, double *lu, double *y) {
+    int st = orc_ilu0(n, rp, ci, a, lu);
+    if (st) return st;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t c = 0; c < k; ++c) {
+            double s = b[(int64_t)i * k + c];
+            for (int64_t e = rp[i]; e < rp[i + 1] && ci[e] < i; ++e) s -= lu[e] * y[(int64_t)ci[e] * k + c];
+            y[(int64_t)i * k + c] = s;
+        }
+    return OK;
+}
+
 /* Adjoint of y = M L^-1 b with x = L^-1 b (not in the paper; closed forms):
  * u = M^T gy, lam = L^-T u, gb = lam, gL_ij = -sum_c lam_ic x_jc on pattern(L),
  * gM_ij = sum_c gy_ic x_jc on pattern(M). gL, gM may be NULL. */

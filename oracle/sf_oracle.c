@@ -16,7 +16,8 @@
  * Conventions: CSR with int32 rowptr[n+1] and colidx[nnz] (ascending within a row),
  * double values in CSR order; dense blocks are n x k row-major.
  * Return codes: 0 on success; -(i+1) for a missing or zero diagonal at row i;
- * +(i+1) for an incomplete-Cholesky breakdown (non-positive pivot) at row i.
+ * +(i+1) for an incomplete-Cholesky breakdown (non-positive pivot) at row i, or for a zero
+ * incomplete-LU pivot u_ii.
  */
 #include <math.h>
 #include <stdint.h>

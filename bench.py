@@ -104,19 +104,23 @@ def make_workload(name, dtype_name):
         adj_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec + es * (nnzL + nnzM)
         # fused adjoint kernel alone: L^T and M^T (pattern, values), gy in, lam out
         adj_exec_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 2 * vec
-        fwd_flops = 2 * (nnzL + nnzM) * k
+        fwd_flops = 2 * (nnzL + nnzM) * k + n * k                                # + one division per row
+        adj_flops = 2 * (nnzL + nnzM) * k + n * k
     elif w.pair == "spmv_trsv":
         fwd_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec      # x_in, b in, z out
         adj_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 5 * vec + es * (nnzL + nnzM)
         # fused adjoint kernel alone: L^T and A^T (pattern, values), gz in, lam and gx out
         adj_exec_bytes = csr_bytes(nnzL, n, es) + csr_bytes(nnzM, n, es) + 3 * vec
-        fwd_flops = 2 * (nnzL + nnzM) * k
+        fwd_flops = 2 * (nnzL + nnzM) * k + n * k
+        adj_flops = 2 * (nnzL + nnzM) * k + n * k
     else:  # ic0_trsv: read tril(A) values + pattern, write factor values, b in, y out
         fwd_bytes = csr_bytes(nnzL, n, es) + es * nnzL + 2 * vec
         adj_bytes = adj_exec_bytes = 0
-        fwd_flops = 2 * nnzL * k + 4 * nnzL
+        fwd_flops = 2 * nnzL * k + n * k + 4 * nnzL    # solve; factor: divide, square, sum per entry
+        adj_flops = 0
     return dict(w=w, name=name, pair=w.pair, n=n, k=k, nnzL=nnzL, nnzM=nnzM, adj=adj, es=es,
                 fwd_bytes=fwd_bytes, adj_bytes=adj_bytes, adj_exec_bytes=adj_exec_bytes, fwd_flops=fwd_flops,
+                adj_flops=adj_flops,
                 fits_l2=(fwd_bytes < 129e6))
 
 
@@ -310,6 +314,24 @@ def t_hop_ns(torch, device):
     return ms / 3 * 1e6 / n
 
 
+# ----------------------------------------------------------------------------- bounds
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal; nothing here measures it)
+
+
+def roofline_bounds(depth, t_hop_ns, nbytes, hbm_gbs, flops, dtype, kernel_ms):
+    """Lower bounds on one launch of the executor kernel, in ms: the dependence chain
+    (depth x one hop), the HBM stream of its algorithmic bytes, and for FP64 its algorithmic
+    flops at the nominal FP64 rate; the tightest of them and the fraction of it achieved."""
+    b = {"latency": depth * t_hop_ns * 1e-6, "hbm": nbytes / (hbm_gbs * 1e9) * 1e3}
+    if dtype == "f64" and flops:
+        b["fp64"] = flops / (FP64_NOMINAL_TFLOPS * 1e12) * 1e3
+    tight = max(b, key=b.get)
+    return {"latency_bound_ms": b["latency"], "hbm_bound_ms": b["hbm"], "fp64_bound_ms": b.get("fp64"),
+            "fp64_peak_tflops": FP64_NOMINAL_TFLOPS if "fp64" in b else None, "fp64_peak_source": "nominal",
+            "algorithmic_flops_per_launch": flops, "tightest_bound": tight,
+            "frac_of_tightest_bound": b[tight] / kernel_ms if kernel_ms > 0 else None}
+
+
 # ----------------------------------------------------------------------------- ranks
 def max_over_ranks(x, world, device):
     """The largest of one float per rank, on every rank (torch.distributed, any backend);
@@ -496,8 +518,8 @@ def run_gpu(args):
             "traffic": traffic,
             "peak_source": peak_src,
             "algorithmic_bytes_per_launch": dom_bytes,
-            "latency_bound_ms": depth * thop * 1e-6,
-            "hbm_bound_ms": dom_bytes / (hbm * 1e9) * 1e3,
+            **roofline_bounds(depth, thop, dom_bytes, hbm, wl["fwd_flops"] if dom == "fwd" else wl["adj_flops"],
+                              args.dtype, dom_ms),
         },
         "fwd_ms": fwd_ms,
         "adj_ms": adj_ms,

@@ -29,7 +29,7 @@ def test_adjoint_trsv_spmv(dtype, k, ef, lpr):
     gL, gM = torch.empty_like(Lv), torch.empty_like(Mv)
     gb = sch.adjoint(Lv, Mv, t(w.gy, dtype), saved=xs, gL=gL, gM=gM)
     sch.check()
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     assert col_rel_err(host(gb), gb_ref) < tol
     assert vec_rel_err(host(gL), gL_ref) < tol
     assert vec_rel_err(host(gM), gM_ref) < tol
@@ -52,7 +52,7 @@ def test_adjoint_spmv_trsv(dtype, k, ef, lpr):
     gx, gL, gA = torch.empty_like(xin), torch.empty_like(Lv), torch.empty_like(Av)
     gb = sch.adjoint(Lv, Av, t(w.gy, dtype), saved=z, x_in=xin, gx=gx, gL=gL, gM=gA)
     sch.check()
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     assert col_rel_err(host(gb), gb_ref) < tol
     assert col_rel_err(host(gx), gx_ref) < tol
     assert vec_rel_err(host(gL), gL_ref) < tol

@@ -32,7 +32,7 @@ def test_batched_forward_adjoint_and_graph(dtype):
     gb = sch.adjoint(Lv, Mv, gy, saved=xs, gL=gL, gM=gM)
     sch.check()
     off, offL, offM = 0, 0, 0
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     for x in w.instances:
         xr, yr = oracle.trsv_spmv(x.L, x.M, x.b)
         gbr, gLr, gMr = oracle.adj_trsv_spmv(x.L, x.M, xr, x.gy)

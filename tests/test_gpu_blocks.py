@@ -67,7 +67,7 @@ def test_trsv_spmv_blocks_forward_adjoint(dtype, lanes, B):
     gL, gM = torch.empty_like(Lv), torch.empty_like(Mv)
     gb = sch.adjoint(Lv, Mv, gy, saved=xs, gL=gL, gM=gM)
     sch.check()
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     assert col_rel_err(host(xs), x_ref) < TOL[dtype]
     assert col_rel_err(host(y), y_ref) < TOL[dtype]
     assert col_rel_err(host(gb), gb_ref) < tol
@@ -88,7 +88,7 @@ def test_spmv_trsv_blocks_forward_adjoint(dtype, lanes, B):
     gx, gL, gA = torch.empty_like(xin), torch.empty_like(Lv), torch.empty_like(Av)
     gb = sch.adjoint(Lv, Av, t(w.gy, dtype), saved=z, x_in=xin, gx=gx, gL=gL, gM=gA)
     sch.check()
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     assert col_rel_err(host(z), z_ref) < TOL[dtype]
     assert col_rel_err(host(gb), gb_ref) < tol and col_rel_err(host(gx), gx_ref) < tol
     assert vec_rel_err(host(gL), gL_ref) < tol and vec_rel_err(host(gA), gA_ref) < tol
@@ -173,7 +173,7 @@ def test_ws_trsv_spmv_forward_adjoint(mode, dtype, B, g2):
         gL, gM = torch.empty_like(Lv), torch.empty_like(Mv)
         gb = sch.adjoint(Lv, Mv, gy, saved=xs, gL=gL, gM=gM)
         sch.check()
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     assert col_rel_err(host(xs), x_ref) < TOL[dtype]
     assert col_rel_err(host(y), y_ref) < TOL[dtype]
     assert col_rel_err(host(gb), gb_ref) < tol

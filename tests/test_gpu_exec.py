@@ -58,7 +58,7 @@ def test_ic0_trsv(dtype, k, lpr):
     y = sch.execute(t(w.L.vals, dtype), b=t(w.b, dtype), x_save=lf)
     sch.check()
     assert vec_rel_err(host(lf), lf_ref) < TOL[dtype]
-    assert col_rel_err(host(y), y_ref) < TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    assert col_rel_err(host(y), y_ref) < TOL[dtype]
 
 
 def test_ic0_with_intersections_and_alone():
@@ -149,7 +149,7 @@ def test_ic0_occupancy_variant(dtype):
     y = sch.execute(t(w.L.vals, dtype), b=t(w.b, dtype), x_save=lf)
     sch.check()
     assert vec_rel_err(host(lf), lf_ref) < TOL[dtype]
-    assert col_rel_err(host(y), y_ref) < TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    assert col_rel_err(host(y), y_ref) < TOL[dtype]
 
 
 def test_ic0_pairs_setter_rejects_other_pairs():

@@ -80,7 +80,7 @@ def test_batched512_forward_adjoint_full(dtype):
     gb = sch.adjoint(Lv, Mv, gy, saved=xs, gL=gL, gM=gM)
     sch.check()
     y, gb, gL, gM = host(y), host(gb), host(gL), host(gM)
-    tol = TOL[dtype] * (10 if dtype == torch.float32 else 1)
+    tol = TOL[dtype]
     off = offL = offM = 0
     worst = 0.0
     for x in w.instances:

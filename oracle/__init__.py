@@ -31,7 +31,8 @@ _lib = None
 # schedule kinds of sf_oracle.c
 SEP, PAIRED, PAIRED_T, SEP_T = 0, 1, 2, 3
 # cost formulas of orc_costs
-COST_SEP, COST_PAIRED_T, COST_SEP_T, COST_SPMV_TRSV, COST_IC0_TRSV, COST_TRSV, COST_IC0 = range(7)
+(COST_SEP, COST_PAIRED_T, COST_SEP_T, COST_SPMV_TRSV, COST_IC0_TRSV, COST_TRSV, COST_IC0, COST_TRSV_TRSV,
+ COST_ILU0_TRSV) = range(9)
 
 
 class OracleError(RuntimeError):

@@ -352,11 +352,15 @@ int orc_levels(int32_t kind, int32_t n, const int32_t *lrp, const int32_t *lci,
  *   PAIRED (SpIC0->SpTRSV, kernel 4): 2 nnz(L_i) + sum_{j in L_i, j<i} nnz(L_j) + 1
  *   PAIRED (SpTRSV alone, kernel 5): nnz(L_i) + 1
  *   PAIRED (SpIC0 alone, kernel 6): nnz(L_i) + sum_{j in L_i, j<i} nnz(L_j) + 1
+ *   PAIRED (SpTRSV->SpTRSV, kernel 7): 2 nnz(L_i) + 1 (the row is read by both solves)
+ *   PAIRED (SpILU0->SpTRSV, kernel 8, M = A, L = tril(A)):
+ *          nnz(A_i) + sum_{j in L_i, j<i} nnz(A_j) + nnz(L_i) + 1
  *   PAIRED_T (kernel 2): nnz(M^T_j) + nnz(L^T_j) + 1
  *   SEP_T  tag 0: nnz(L^T_j) + 1      tag 1: nnz(A^T_j) + 1
  * (the adjoint's value gradients are a separate streaming pass, not part of these items)
  * `what` selects the formula: 0 SEP, 1 PAIRED_T, 2 SEP_T, 3 SpMV->SpTRSV,
- * 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0. Output cost[v] for every vertex. */
+ * 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0, 7 SpTRSV->SpTRSV, 8 SpILU0->SpTRSV. Output cost[v]
+ * for every vertex. */
 int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, const int32_t *mrp,
               const int32_t *mci, int64_t *cost) {
     int64_t *colL = NULL, *colM = NULL;
@@ -374,6 +378,9 @@ int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, c
         if (what == 4 || what == 6)
             for (int64_t e = lrp[i]; e < lrp[i + 1]; ++e)
                 if (lci[e] < i) s += lrp[lci[e] + 1] - lrp[lci[e]];
+        if (what == 8) /* rows k of A that row i of SpILU0 eliminates with */
+            for (int64_t e = lrp[i]; e < lrp[i + 1]; ++e)
+                if (lci[e] < i) s += mrp[lci[e] + 1] - mrp[lci[e]];
         switch (what) {
             case 0: cost[i] = nl + 1; cost[n + i] = nm + 1; break;
             case 1: cost[i] = colM[i] + colL[i] + 1; break;
@@ -382,6 +389,8 @@ int orc_costs(int32_t what, int32_t n, const int32_t *lrp, const int32_t *lci, c
             case 4: cost[i] = 2 * nl + s + 1; break;
             case 5: cost[i] = nl + 1; break;
             case 6: cost[i] = nl + s + 1; break;
+            case 7: cost[i] = 2 * nl + 1; break;
+            case 8: cost[i] = nm + s + nl + 1; break;
             default: free(colL); free(colM); return -1;
         }
     }
@@ -579,6 +588,12 @@ double orc_reuse_ratio(int32_t pair, int64_t n, int64_t size_L, int64_t size_M) 
         case 2: /* y shared: 2n / max(size_M + 2n, size_L + 2n) */
             a = (double)(size_M + 2 * n); b = (double)(size_L + 2 * n);
             return (double)(2 * n) / (a > b ? a : b);
+        case 5: /* combination 1, L and x shared: (2n + 2 size_L) / max(2n + size_L, size_L + 2n) */
+            a = (double)(2 * n + size_L); b = (double)(size_L + 2 * n);
+            return (double)(2 * n + 2 * size_L) / (a > b ? a : b);
+        case 6: /* combination 6, A shared: 2 size_A / max(size_A, size_L + 2n), size_M = size_A */
+            a = (double)size_M; b = (double)(size_L + 2 * n);
+            return (double)(2 * size_M) / (a > b ? a : b);
         default: return -1.0;
     }
 }

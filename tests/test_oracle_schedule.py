@@ -139,6 +139,12 @@ def test_costs_hand_computed():
     # column counts: L^T rows 3,2,1; M^T rows 1,1,2
     assert oracle.costs(oracle.COST_PAIRED_T, L, M).tolist() == [1 + 3 + 1, 1 + 2 + 1, 2 + 1 + 1]
     assert oracle.costs(oracle.COST_SEP_T, L, M).tolist() == [3 + 1, 2 + 1, 1 + 1, 2, 2, 3]
+    # SpTRSV -> SpTRSV reads the row of L twice
+    assert oracle.costs(oracle.COST_TRSV_TRSV, L).tolist() == [3, 5, 7]
+    # SpILU0 -> SpTRSV on A = [[1,0,1],[1,1,0],[1,1,1]], L = tril(A): row i of A, the rows of A
+    # it eliminates with (none; row 0; rows 0 and 1), the solve row: 2+0+1+1, 2+2+2+1, 3+4+3+1
+    Ad = np.array([[1.0, 0, 1], [1, 1, 0], [1, 1, 1]])
+    assert oracle.costs(oracle.COST_ILU0_TRSV, dense_to_csr(np.tril(Ad)), dense_to_csr(Ad)).tolist() == [4, 7, 11]
 
 
 def test_partition_isolates_wide_items():

@@ -54,10 +54,23 @@ typedef enum {
  *                F = I: row i of the solve waits for row i of the factor.
  *  SF_SPMV_TRSV  combination 2: r = b - A x_in (SpMV), then z = L^-1 r with L = tril(A)
  *                passed as its own CSR (one Gauss-Seidel half-sweep). F = I.
+ *  SF_TRSV_TRSV  combination 1: x = L^-1 b, then z = L^-1 x with the same L. F = I.
+ *  SF_ILU0_TRSV  combination 6: L U ~ A by zero fill-in ILU (SpILU0, row-oriented IKJ form on
+ *                A's pattern, L unit lower), then y = L^-1 b. F = I. sf_inspect takes L =
+ *                the pattern of tril(A) (the DAG) and M = A (square, every diagonal present,
+ *                at most 256 entries per row).
  * Single-kernel schedules, the building blocks of the unfused two-launch path:
  *  SF_TRSV       x = L^-1 b alone.
  *  SF_IC0        the zero fill-in IC factor alone.                                      */
-typedef enum { SF_TRSV_SPMV = 0, SF_IC0_TRSV = 1, SF_SPMV_TRSV = 2, SF_TRSV = 3, SF_IC0 = 4 } sf_pair;
+typedef enum {
+    SF_TRSV_SPMV = 0,
+    SF_IC0_TRSV = 1,
+    SF_SPMV_TRSV = 2,
+    SF_TRSV = 3,
+    SF_IC0 = 4,
+    SF_TRSV_TRSV = 5,
+    SF_ILU0_TRSV = 6
+} sf_pair;
 
 typedef enum { SF_F64 = 0, SF_F32 = 1 } sf_dtype;
 
@@ -126,23 +139,29 @@ sf_status sf_inspect_batched(sf_pair pair, int32_t count, const sf_csr *Ls, cons
                              const sf_options *opt, void *stream, sf_schedule **out);
 
 /* Executor (§2.3): one persistent launch that runs the fused schedule.
- *  L_vals: SF_TRSV_SPMV, SF_SPMV_TRSV, SF_TRSV: values of L; SF_IC0_TRSV, SF_IC0: the
- *          values of tril(A) to factor (input, not modified).
- *  M_vals: SF_TRSV_SPMV: values of M; SF_SPMV_TRSV: values of A; otherwise NULL.
+ *  L_vals: SF_TRSV_SPMV, SF_SPMV_TRSV, SF_TRSV, SF_TRSV_TRSV: values of L; SF_IC0_TRSV, SF_IC0:
+ *          the values of tril(A) to factor (input, not modified); SF_ILU0_TRSV: NULL.
+ *          SF_SPMV_TRSV accepts NULL when L's pattern is tril(A)'s (checked at inspection) and
+ *          SF_EPOCH_FLAGS is off: L = tril(A) is then read from A's rows (shared storage, one
+ *          pass over A's row gives both r_i and the solve's sum).
+ *  M_vals: SF_TRSV_SPMV: values of M; SF_SPMV_TRSV, SF_ILU0_TRSV: values of A; otherwise NULL.
  *  x_in:   SF_SPMV_TRSV only: the SpMV operand (n x k); otherwise NULL.
  *  b:      right-hand side (n x k); NULL for SF_IC0.
- *  y:      result (n x k): y = M L^-1 b, y = L^-1 b (IC0 factor L), z = L^-1 (b - A x_in),
- *          or x = L^-1 b for SF_TRSV; NULL for SF_IC0.
- *  x_save: optional. SF_TRSV_SPMV: receives the intermediate x = L^-1 b (n x k), needed by
- *          sf_adjoint. SF_IC0_TRSV / SF_IC0: receives the factor values on L's pattern
- *          (required for SF_IC0). When NULL a library-owned buffer is used; it is
- *          allocated on the first call that needs it, so make one such call before
- *          capturing the stream into a CUDA graph.
- *  k:      number of right-hand sides, 1 <= k <= 1024. With k = 1 (unless SF_EPOCH_FLAGS
- *          was given) the vector that carries the dependences (x_save or its library-owned
- *          stand-in for SF_TRSV_SPMV, y for SF_TRSV and SF_SPMV_TRSV) is first filled with
- *          the all-ones pattern on `stream`; a result whose bits equal that pattern is
- *          stored as the canonical NaN instead (both are NaN).
+ *  y:      result (n x k): y = M L^-1 b, y = L^-1 b (IC0 or ILU0 factor L), z = L^-1 (b - A x_in),
+ *          z = L^-1 L^-1 b for SF_TRSV_TRSV, or x = L^-1 b for SF_TRSV; NULL for SF_IC0.
+ *  x_save: optional. SF_TRSV_SPMV, SF_TRSV_TRSV: receives the intermediate x = L^-1 b (n x k),
+ *          needed by sf_adjoint. SF_IC0_TRSV / SF_IC0: receives the factor values on L's pattern
+ *          (required for SF_IC0). SF_ILU0_TRSV: receives the factor on A's pattern (the strictly
+ *          lower part of the unit lower L, then U with its diagonal). When NULL a library-owned
+ *          buffer is used; it is allocated on the first call that needs it, so make one such
+ *          call before capturing the stream into a CUDA graph.
+ *  k:      number of right-hand sides, 1 <= k <= 1024. Unless SF_EPOCH_FLAGS was given, the
+ *          vectors that carry the dependences (x_save or its library-owned stand-in for
+ *          SF_TRSV_SPMV and SF_TRSV_TRSV, y for SF_TRSV, SF_SPMV_TRSV, SF_TRSV_TRSV, SF_IC0_TRSV
+ *          and SF_ILU0_TRSV, the factor for the IC0 and ILU0 pairs) are first filled with the
+ *          all-ones pattern on `stream` and every value is published by its own store; a
+ *          result whose bits equal that pattern is stored as the canonical NaN instead (both
+ *          are NaN). SF_ILU0_TRSV always publishes values this way.
  * Concurrent calls with the same schedule on different streams race; calls on one
  * stream are ordered. Returns after enqueueing the launch. */
 sf_status sf_execute(const sf_schedule *sch, sf_dtype dt, int32_t k, const void *L_vals,

@@ -108,6 +108,8 @@ double reuse_ratio(sf_pair pair, long long n, long long sl, long long sm) {
         case SF_TRSV_SPMV: return (double)(2 * n) / (double)std::max(sl + 2 * n, sm + 2 * n);
         case SF_IC0_TRSV: return (double)(2 * sl) / (double)std::max(sl, sl + 2 * n);
         case SF_SPMV_TRSV: return (double)(2 * n) / (double)std::max(sm + 2 * n, sl + 2 * n);
+        case SF_TRSV_TRSV: return (double)(2 * n + 2 * sl) / (double)std::max(2 * n + sl, sl + 2 * n);
+        case SF_ILU0_TRSV: return (double)(2 * sm) / (double)std::max(sm, sl + 2 * n);
         default: return 0.0;
     }
 }
@@ -144,6 +146,10 @@ struct sf_schedule {
     long long ic0_npairs = 0;
     bool ic0_use_pairs = true;
     void *ic0_rinv = nullptr;   // 1 / L_ii of the factor, n values of the widest element type
+    // pairs with A (SpMV -> SpTRSV, SpILU0 -> SpTRSV): position of the diagonal in each row of A,
+    // and whether L's pattern is tril(A)'s (then SpMV -> SpTRSV may read L from A's storage)
+    int *a_diag = nullptr;
+    bool tril_ok = false;
     std::mutex mu;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -171,8 +177,8 @@ sf_status validate_options(const sf_options *o) {
     return SF_OK;
 }
 
-bool pair_has_M(sf_pair p) { return p == SF_TRSV_SPMV || p == SF_SPMV_TRSV; }
-bool pair_valid(sf_pair p) { return p >= SF_TRSV_SPMV && p <= SF_IC0; }
+bool pair_has_M(sf_pair p) { return p == SF_TRSV_SPMV || p == SF_SPMV_TRSV || p == SF_ILU0_TRSV; }
+bool pair_valid(sf_pair p) { return p >= SF_TRSV_SPMV && p <= SF_ILU0_TRSV; }
 
 sf_status check_csr_args(const sf_csr *m, const char *name, bool square) {
     if (!m) return fail(SF_ERR_INVALID_ARG, "%s is NULL", name);
@@ -371,6 +377,23 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
             return fail(SF_ERR_BAD_PATTERN, "M: %s (row %d)", pat_name((unsigned)(pst >> 32)), (int)(pst & 0xffffffffu));
     }
     const bool want_adj = (o.flags & SF_WANT_ADJOINT) != 0;
+    if (S->pair == SF_SPMV_TRSV || S->pair == SF_ILU0_TRSV) {
+        S->a_diag = (int *)S->keep.alloc(sizeof(int) * (size_t)S->n);
+        if (!S->a_diag) return fail(SF_ERR_OOM, "inspector: out of device memory");
+        unsigned bad = 0;
+        SF_CK(tril_map(S->M, S->L, S->a_diag, &bad, s, tmp), "diagonal positions of A");
+        S->tril_ok = bad == 0;
+        if (S->pair == SF_ILU0_TRSV) {
+            if (bad & 1u) return fail(SF_ERR_BAD_PATTERN, "A: a row misses its diagonal");
+            if (bad & 2u) return fail(SF_ERR_BAD_PATTERN, "L must be the pattern of tril(A)");
+            std::vector<int> rp((size_t)S->n + 1);
+            SF_CK(cudaMemcpy(rp.data(), S->M.rowptr, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost), "inspector");
+            for (int i = 0; i < S->n; ++i)
+                if (rp[i + 1] - rp[i] > kIluMaxRow)
+                    return fail(SF_ERR_UNSUPPORTED, "ILU0 rows of A hold at most %d entries (row %d has %d)", kIluMaxRow,
+                                i, rp[i + 1] - rp[i]);
+        }
+    }
     SF_CK(transpose_csr(S->L, S->LT, s, tmp, S->keep), "transpose of L");
     S->hasLT = true;
     if (S->pair == SF_TRSV_SPMV || (S->pair == SF_SPMV_TRSV && want_adj)) {
@@ -400,6 +423,8 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
         case SF_SPMV_TRSV: kind = K_PAIRED; what = 3; break;
         case SF_TRSV: kind = K_PAIRED; what = 5; break;
         case SF_IC0: kind = K_PAIRED; what = 6; break;
+        case SF_TRSV_TRSV: kind = K_PAIRED; what = 7; break;
+        case SF_ILU0_TRSV: kind = K_PAIRED; what = 8; break;
     }
     S->packing = (kind == K_SEP) ? 0 : 1;
     sf_status st = build_dir(S, S->fwd, kind, what, o.part_cost_target, s, tmp);
@@ -485,6 +510,7 @@ int occupancy(int mode, int dtype, int lpr, bool vf, int team, int minb) {
     int &c = cache[mode][dtype][li][vf ? 1 : 0][team == 8 ? 0 : 1][minb > 1 ? 1 : 0];
     if (!c) {
         if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf, team, minb);
+        else if (mode == M_TRSV_TRSV || mode == M_ILU0_TRSV) c = occupancy_next(mode, dtype, lpr, vf, team, minb);
         else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
             c = occupancy_adj(mode, dtype, lpr, vf, team, minb);
         else c = occupancy_pair(mode, dtype, lpr, vf, team, minb);
@@ -496,6 +522,7 @@ int occupancy(int mode, int dtype, int lpr, bool vf, int team, int minb) {
 void *value_flag_buffer(int mode, const ExecArgs &a) {
     switch (mode) {
         case M_TRSV_SPMV: return a.xs;
+        case M_TRSV_TRSV: return a.xs;
         case M_TRSV:
         case M_SPMV_TRSV: return a.y;
         case M_ADJ_TRSV_SPMV:
@@ -534,15 +561,24 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     a.ic0_pp = S->ic0_use_pairs ? S->ic0_pp : nullptr;
     a.ic0_pairs = S->ic0_use_pairs ? S->ic0_pairs : nullptr;
     a.ic0_rinv = S->ic0_rinv;
+    a.a_diag = S->a_diag;
     const int dtype = dt == SF_F64 ? 0 : 1;
     void *vbuf = value_flag_buffer(mode, a);
     const bool ic0 = mode == M_IC0_TRSV || mode == M_IC0;
     // IC0 rows publish through their values when the pair lists exist (any k; the flat
     // index row * k + column of y must fit in an int)
     const bool vf = ic0 ? (!S->epoch_flags && a.ic0_pp != nullptr && (long long)S->n * k <= 0x7fffffffLL)
-                        : (k == 1 && !S->epoch_flags && vbuf != nullptr);
+                        : (!S->epoch_flags && vbuf != nullptr && (long long)S->n * k <= 0x7fffffffLL &&
+                           (k == 1 || lpr >= 16));
+    // shared storage (SpMV -> SpTRSV with L read from A's rows) is a partition-executor path
+    // that publishes through values
+    const bool shared = mode == M_SPMV_TRSV && a.Lv == nullptr;
+    if (shared && !vf)
+        return fail(SF_ERR_UNSUPPORTED, "L read from A's rows needs value flags: k = 1, or at least 16 lanes per row");
+    // the row-block executors serve one right-hand side
+    const bool rows1 = vf && !ic0 && k == 1 && !shared;
     // row-block executor with packed records and bulk copies
-    if (vf && !ic0 && d.exec_mode == 4 && d.nb > 0) {
+    if (rows1 && d.exec_mode == 4 && d.nb > 0) {
         const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
         const int rows = std::min(d.B, S->n);
         const int occ = block_tma_fits(mode, dtype, rows, nc);
@@ -569,7 +605,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         return SF_OK;
     }
     // warp-specialised row-block executor
-    if (vf && !ic0 && d.exec_mode == 3 && d.nb > 0) {
+    if (rows1 && d.exec_mode == 3 && d.nb > 0) {
         // consumer threads: one per position of the widest segment, a power of two in [32, 256]
         const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
         const int rows = std::min(d.B, S->n);
@@ -592,7 +628,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     }
     // the row-block executor serves one right-hand side with value flags (its pre-pass
     // resets the published vector)
-    if (vf && !ic0 && d.exec_mode == 2 && d.nb > 0) {
+    if (rows1 && d.exec_mode == 2 && d.nb > 0) {
         const int threads = block_threads(d);
         const int occ = block_exec_occupancy(mode, dtype, d.blpr, std::min(d.B, S->n), threads);
         if (occ > 0) {
@@ -615,7 +651,13 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         }
         return fail(SF_ERR_UNSUPPORTED, "row blocks of %d rows do not fit in shared memory", d.B);
     }
-    if (vf && ic0) {
+    const bool ilu0 = mode == M_ILU0_TRSV;
+    if (ilu0) {
+        // value flags only: the factor and y start as the all-ones pattern; whole-warp rows
+        const size_t es = dt == SF_F64 ? 8 : 4;
+        SF_CK(cudaMemsetAsync(a.y, 0xff, es * (size_t)S->n * (size_t)k, s), "value-flag reset");
+        SF_CK(cudaMemsetAsync(a.xs, 0xff, es * (size_t)S->M.nnz, s), "value-flag reset");
+    } else if (vf && ic0) {
         // value-flag reset (all bits set): y, 1 / L_ii, and the factor when pairs read it
         const size_t es = dt == SF_F64 ? 8 : 4;
         if (a.y) SF_CK(cudaMemsetAsync(a.y, 0xff, es * (size_t)S->n * (size_t)k, s), "value-flag reset");
@@ -624,13 +666,18 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     } else if (vf) {
         // value-flag reset and reciprocal diagonals in one pass
         a.rdiag = d.aux;
-        SF_CK(launch_rdiag(dtype, S->n, S->L.rowptr, a.Lv, vbuf, d.aux, d.st, s), "value-flag reset");
+        // shared storage: the diagonal of L is A's
+        SF_CK(launch_rdiag(dtype, S->n, k, S->L.rowptr, shared ? a.Mv : a.Lv, vbuf, d.aux, d.st, s,
+                           shared ? S->a_diag : nullptr, mode == M_TRSV_TRSV ? a.y : nullptr),
+              "value-flag reset");
     }
     const int minb = d.minb;
-    int per_sm = occupancy(mode, dtype, lpr, vf, team, minb);
+    const int lpr_l = ilu0 ? 32 : lpr, team_l = ilu0 ? 32 : team;
+    const bool vf_l = ilu0 ? true : vf;
+    int per_sm = occupancy(mode, dtype, lpr_l, vf_l, team_l, minb);
     if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
     long long blocks = (long long)per_sm * S->sms;
-    const long long teams_per_block = 8LL * (32 / team);
+    const long long teams_per_block = 8LL * (32 / team_l);
     blocks = std::min<long long>(blocks, ((long long)d.n_parts + teams_per_block - 1) / teams_per_block);
     blocks = std::max<long long>(blocks, 1);
     // two partition classes when a split is set: split_pct percent of the teams run the
@@ -647,6 +694,8 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     cudaError_t e;
     if (d.ev_start) SF_CK(cudaEventRecord(d.ev_start, s), "timing event");
     if (mode == M_TRSV_SPMV || mode == M_TRSV) e = launch_exec_fwd(mode, dtype, lpr, vf, team, minb, (int)blocks, s, a);
+    else if (mode == M_TRSV_TRSV || mode == M_ILU0_TRSV)
+        e = launch_exec_next(mode, dtype, lpr_l, vf_l, team_l, minb, (int)blocks, s, a);
     else if (mode == M_ADJ_TRSV_SPMV || mode == M_ADJ_SPMV_TRSV)
         e = launch_exec_adj(mode, dtype, lpr, vf, team, minb, (int)blocks, s, a);
     else e = launch_exec_pair(mode, dtype, lpr, vf, team, minb, (int)blocks, s, a);
@@ -750,7 +799,8 @@ SF_API sf_status sf_execute(const sf_schedule *S, sf_dtype dt, int32_t k, const 
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (dt != SF_F64 && dt != SF_F32) return fail(SF_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
     if (k < 1 || k > 1024) return fail(SF_ERR_INVALID_ARG, "k must be in [1, 1024]");
-    if (!L_vals) return fail(SF_ERR_INVALID_ARG, "L_vals is NULL");
+    if (!L_vals && S->pair != SF_SPMV_TRSV && S->pair != SF_ILU0_TRSV)
+        return fail(SF_ERR_INVALID_ARG, "L_vals is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t es = dt == SF_F64 ? 8 : 4;
     ExecArgs a{};
@@ -773,7 +823,28 @@ SF_API sf_status sf_execute(const sf_schedule *S, sf_dtype dt, int32_t k, const 
             break;
         case SF_SPMV_TRSV:
             if (!M_vals || !x_in || !b || !y) return fail(SF_ERR_INVALID_ARG, "SF_SPMV_TRSV needs M_vals, x_in, b and y");
+            if (!L_vals && (!S->tril_ok || S->epoch_flags))
+                return fail(SF_ERR_INVALID_ARG, "L_vals may be NULL (L read from A) only when L's pattern is tril(A)'s "
+                                                "and rows publish through their values");
             mode = M_SPMV_TRSV;
+            break;
+        case SF_TRSV_TRSV:
+            if (!b || !y) return fail(SF_ERR_INVALID_ARG, "SF_TRSV_TRSV needs b and y");
+            if (M_vals || x_in) return fail(SF_ERR_INVALID_ARG, "M_vals and x_in must be NULL for SF_TRSV_TRSV");
+            mode = M_TRSV_TRSV;
+            if (!x_save) {
+                sf_status st = get_scratch(S, (size_t)S->n * k * es, s, &a.xs);
+                if (st != SF_OK) return st;
+            }
+            break;
+        case SF_ILU0_TRSV:
+            if (!M_vals || !b || !y) return fail(SF_ERR_INVALID_ARG, "SF_ILU0_TRSV needs M_vals (A), b and y");
+            if (L_vals || x_in) return fail(SF_ERR_INVALID_ARG, "L_vals and x_in must be NULL for SF_ILU0_TRSV");
+            mode = M_ILU0_TRSV;
+            if (!x_save) {
+                sf_status st = get_scratch(S, (size_t)S->M.nnz * es, s, &a.xs);
+                if (st != SF_OK) return st;
+            }
             break;
         case SF_IC0_TRSV:
             if (!b || !y) return fail(SF_ERR_INVALID_ARG, "SF_IC0_TRSV needs b and y");
@@ -1137,13 +1208,18 @@ SF_API sf_status sf_schedule_launches(const sf_schedule *S, int32_t which, int32
     if (k < 1) return fail(SF_ERR_INVALID_ARG, "k must be >= 1");
     const Dir &d = which ? S->adj : S->fwd;
     if (!d.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
-    const bool vf_pair = S->pair == SF_TRSV_SPMV || S->pair == SF_SPMV_TRSV || S->pair == SF_TRSV;
-    const bool vf = k == 1 && !S->epoch_flags && vf_pair;
+    const bool vf_pair = S->pair == SF_TRSV_SPMV || S->pair == SF_SPMV_TRSV || S->pair == SF_TRSV ||
+                         S->pair == SF_TRSV_TRSV;
+    // the same choice as launch(): values publish rows for k = 1, or for any k with 16 or more
+    // lanes per row
+    const int kt = S->kt ? std::min(S->kt, 32) : std::min(pow2_ceil(k), 32);
+    const int lpr = std::max(d.lpr, kt);
+    const bool vf = !S->epoch_flags && vf_pair && (long long)S->n * k <= 0x7fffffffLL && (k == 1 || lpr >= 16);
     int n = 0;
-    if (vf && d.exec_mode >= 2 && d.nb > 0) n = 2 + (d.exec_mode == 4 ? 1 : 0);   // pre-pass(es) + executor
+    if (vf && k == 1 && d.exec_mode >= 2 && d.nb > 0) n = 2 + (d.exec_mode == 4 ? 1 : 0);   // pre-pass(es) + executor
     else n = (vf ? 1 : 0) + 1;                                                  // value-flag reset + executor
     if (which == 1) {
-        const bool mt_direct = S->pair == SF_TRSV_SPMV && vf && d.exec_mode >= 2;
+        const bool mt_direct = S->pair == SF_TRSV_SPMV && vf && k == 1 && d.exec_mode >= 2;
         n += 1 + (mt_direct ? 0 : 1) + 2;   // value gathers and both gradient passes
     }
     *count = n;

@@ -34,6 +34,7 @@
 namespace sf {
 
 constexpr int kUnroll = 4;   // row entries fetched per lane before waiting on them
+constexpr int kExecThreads = 256;   // threads of an executor block
 #ifndef SF_BACKOFF_MIN_NS
 #define SF_BACKOFF_MIN_NS 20
 #endif
@@ -199,6 +200,12 @@ __device__ __forceinline__ unsigned ld_flag_scan(const unsigned *p) {
 constexpr int kPend = 8;
 constexpr int kScanU = 16;
 constexpr int kDataU = 8;
+// Value-flag rows: unset operands noted per lane before the lane waits for them (their flat
+// indices row * k + column fit an int: value flags need n * k < 2^31), and loads in flight per
+// lane: 8 for groups of 16 or more lanes (long rows, any number of right-hand sides), else 4
+// (short rows and one right-hand side; the high-occupancy variants keep to their registers).
+constexpr int kVPend = 4;
+__host__ __device__ constexpr int value_unroll(int lpr) { return lpr >= 16 ? 8 : 4; }
 
 // row_dot with epoch flags, as a sliding window over the lane's slice of the row: a scan reads
 // the flags ahead without fences and notes the first kPend entries whose rows are unpublished,
@@ -288,16 +295,129 @@ __device__ __forceinline__ T row_dot_flags(const int *__restrict__ cols, const i
     return acc;
 }
 
+// Waits for the noted operands of a value-flag dot product (bit q of `pending`: vec[pj[q]] was
+// still the reset pattern) and adds their products; the noted loads are re-issued together.
+template <typename T, int N>
+__device__ __forceinline__ T drain_values(const T *vec, const int (&pj)[N], const T (&pv)[N], unsigned pending,
+                                          ExecState *st, unsigned long long tmo, int row, bool &ok) {
+    T acc = T(0);
+    Waiter w;
+    while (pending) {
+        T xv[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) xv[q] = ((pending >> q) & 1u) ? ld_relaxed_val(vec + pj[q]) : T(0);
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            if (((pending >> q) & 1u) && !is_unset(xv[q])) {
+                acc += pv[q] * xv[q];
+                pending &= ~(1u << q);
+            }
+        if (pending && !w.pause(st, tmo, row)) {
+            ok = false;
+            break;
+        }
+    }
+    return acc;
+}
+
+// row_dot with value flags: every operand vec[cols[e] * k + c] is its own flag (the reset
+// pattern until its producer stores it). A lane streams its slice with VU loads in flight; the
+// loaded operand is the test, so a published entry costs nothing extra and no fence is needed
+// anywhere. VU = 4 (groups of fewer than 16 lanes, k = 1): the unset operands of a chunk are
+// waited for before the next chunk. VU = 8 (groups of 16 or 32 lanes, any k): unset entries are
+// noted (up to kVPend) and the lane moves on; when the list is full, and at the end of the
+// slice, it waits for them together, so a long row does most of its work before its last input
+// exists.
+template <typename T, bool PERM, int VU>
+__device__ __forceinline__ T row_dot_values(const int *__restrict__ cols, const int *__restrict__ perm,
+                                            const T *__restrict__ vals, int e0, int e1, int S, const T *vec, int k,
+                                            int c, bool act, ExecState *st, unsigned long long tmo, int row,
+                                            bool &ok) {
+    T acc = T(0);
+    if constexpr (VU <= 4) {
+        // one right-hand side (the host publishes through values with fewer than 16 lanes per
+        // row only when k = 1), so the operand of entry e is vec[cols[e]]
+        for (int f = e0; f < e1; f += S * VU) {
+            int j[VU];
+            T vv[VU], xv[VU];
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                const int ee = f + u * S;
+                j[u] = -1;
+                vv[u] = T(0);
+                if (ee < e1) {
+                    j[u] = __ldg(cols + ee);
+                    vv[u] = __ldg(vals + (PERM ? __ldg(perm + ee) : ee));
+                }
+            }
+            if (ok) ok = wait_values<T, VU>(vec, j, xv, st, tmo, row);
+#pragma unroll
+            for (int u = 0; u < VU; ++u)
+                if (j[u] >= 0) acc += vv[u] * xv[u];
+        }
+        return acc;
+    } else {
+        if (!act) return acc;
+        int pj[kVPend];
+        T pv[kVPend];
+#pragma unroll
+        for (int q = 0; q < kVPend; ++q) {
+            pj[q] = 0;
+            pv[q] = T(0);
+        }
+        int np = 0;
+        for (int f = e0; f < e1 && ok; f += S * VU) {
+            T vv[VU], xv[VU];
+            int jx[VU];
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                const int ee = f + u * S;
+                vv[u] = T(0);
+                jx[u] = 0;
+                if (ee < e1) {
+                    vv[u] = __ldg(vals + (PERM ? __ldg(perm + ee) : ee));
+                    jx[u] = __ldg(cols + ee) * k + c;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < VU; ++u) xv[u] = (f + u * S < e1) ? ld_relaxed_val(vec + jx[u]) : T(0);
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                if (f + u * S >= e1) continue;
+                if (!is_unset(xv[u])) {
+                    acc += vv[u] * xv[u];
+                    continue;
+                }
+                if (np == kVPend) {
+                    acc += drain_values<T, kVPend>(vec, pj, pv, (1u << kVPend) - 1u, st, tmo, row, ok);
+                    np = 0;
+                }
+#pragma unroll
+                for (int q = 0; q < kVPend; ++q)
+                    if (q == np) {
+                        pj[q] = jx[u];
+                        pv[q] = vv[u];
+                    }
+                ++np;
+            }
+        }
+        if (np > 0 && ok) acc += drain_values<T, kVPend>(vec, pj, pv, (1u << np) - 1u, st, tmo, row, ok);
+        return acc;
+    }
+}
+
 // acc = sum over this lane's slice of entries e in [e0, e1) (stride S) of
 // vals[PERM ? perm[e] : e] * vec[cols[e] * k + c]. D_FLAG / D_VALUE wait for the rows
 // cols[e] first (vec is produced by other warps in this launch).
-template <typename T, int DEP, bool PERM>
+template <typename T, int DEP, bool PERM, int VU = 4>
 __device__ __forceinline__ T row_dot(const int *__restrict__ cols, const int *__restrict__ perm,
                                      const T *__restrict__ vals, int e0, int e1, int S, const T *vec,
                                      int k, int c, bool act, const unsigned *flags, unsigned epoch,
                                      ExecState *st, unsigned long long tmo, int row, bool &ok) {
     if constexpr (DEP == D_FLAG)
         return row_dot_flags<T, PERM>(cols, perm, vals, e0, e1, S, vec, k, c, act, flags, epoch, st, tmo, row, ok);
+    if constexpr (DEP == D_VALUE)
+        return row_dot_values<T, PERM, VU>(cols, perm, vals, e0, e1, S, vec, k, c, act, st, tmo, row, ok);
     if constexpr (DEP == D_NONE) {
         // nothing to wait for: kDataU loads in flight per lane, issued before their products
         T acc = T(0);
@@ -320,40 +440,100 @@ __device__ __forceinline__ T row_dot(const int *__restrict__ cols, const int *__
         }
         return acc;
     }
-    T acc = T(0);
-    for (int e = e0; e < e1; e += S * kUnroll) {
-        int j[kUnroll];
-        T v[kUnroll];
+}
+
+// Gauss-Seidel row with L = tril(A) read from A's own storage (shared storage, value flags):
+// one pass over the lane's slice of A's row gives ax = sum_j A_ij x_in_j over every entry and
+// az = sum_{j<i} A_ij z_j over the entries before the diagonal position dp, each z_j waited for
+// as in row_dot_values (VU = 4: per chunk, one right-hand side; VU = 8: noted when unset and
+// drained when the list fills and at the end).
+template <typename T, int VU>
+__device__ __forceinline__ void gs_row_dot(const int *__restrict__ cols, const T *__restrict__ vals, int e0, int dp,
+                                           int e1, int S, const T *__restrict__ xin, const T *z, int k, int c,
+                                           bool act, ExecState *st, unsigned long long tmo, int row, bool &ok, T &ax,
+                                           T &az) {
+    ax = T(0);
+    az = T(0);
+    if constexpr (VU <= 4) {
+        // one right-hand side (groups of fewer than 16 lanes): chunks of VU entries, the unset
+        // z operands of a chunk waited for before the next chunk
+        for (int f = e0; f < e1; f += S * VU) {
+            int j[VU], jz[VU];
+            T vv[VU], xv[VU], zv[VU];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int ee = e + u * S;
-            j[u] = -1;
-            v[u] = T(0);
-            if (ee < e1) {
-                j[u] = __ldg(cols + ee);
-                v[u] = __ldg(vals + (PERM ? __ldg(perm + ee) : ee));
+            for (int u = 0; u < VU; ++u) {
+                const int ee = f + u * S;
+                j[u] = jz[u] = -1;
+                vv[u] = T(0);
+                if (ee < e1) {
+                    j[u] = __ldg(cols + ee);
+                    vv[u] = __ldg(vals + ee);
+                    if (ee < dp) jz[u] = j[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < VU; ++u) xv[u] = j[u] >= 0 ? __ldg(xin + j[u]) : T(0);
+            if (ok) ok = wait_values<T, VU>(z, jz, zv, st, tmo, row);
+#pragma unroll
+            for (int u = 0; u < VU; ++u) {
+                ax += vv[u] * xv[u];
+                if (jz[u] >= 0) az += vv[u] * zv[u];
             }
         }
-        if constexpr (DEP == D_VALUE) {
-            T xv[kUnroll];
-            if (ok) ok = wait_values<T, kUnroll>(vec, j, xv, st, tmo, row);
+        return;
+    }
+    if (!act) return;
+    int pj[kVPend];
+    T pv[kVPend];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (j[u] >= 0) acc += v[u] * xv[u];
-        } else {
-            if (DEP == D_FLAG && ok) ok = wait_flags<kUnroll>(flags, j, epoch, st, tmo, row);
-            if (act) {
+    for (int q = 0; q < kVPend; ++q) {
+        pj[q] = 0;
+        pv[q] = T(0);
+    }
+    int np = 0;
+    for (int f = e0; f < e1 && ok; f += S * VU) {
+        T vv[VU], xv[VU], zv[VU];
+        int jx[VU];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    if (j[u] >= 0) {
-                        const T xv = DEP == D_FLAG ? __ldcg(vec + (size_t)j[u] * k + c)
-                                                   : __ldg(vec + (size_t)j[u] * k + c);
-                        acc += v[u] * xv;
-                    }
+        for (int u = 0; u < VU; ++u) {
+            const int ee = f + u * S;
+            vv[u] = T(0);
+            jx[u] = 0;
+            if (ee < e1) {
+                vv[u] = __ldg(vals + ee);
+                jx[u] = __ldg(cols + ee) * k + c;
             }
+        }
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int ee = f + u * S;
+            xv[u] = ee < e1 ? __ldg(xin + jx[u]) : T(0);
+            zv[u] = ee < dp ? ld_relaxed_val(z + jx[u]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < VU; ++u) {
+            const int ee = f + u * S;
+            if (ee >= e1) continue;
+            ax += vv[u] * xv[u];
+            if (ee >= dp) continue;
+            if (!is_unset(zv[u])) {
+                az += vv[u] * zv[u];
+                continue;
+            }
+            if (np == kVPend) {
+                az += drain_values<T, kVPend>(z, pj, pv, (1u << kVPend) - 1u, st, tmo, row, ok);
+                np = 0;
+            }
+#pragma unroll
+            for (int q = 0; q < kVPend; ++q)
+                if (q == np) {
+                    pj[q] = jx[u];
+                    pv[q] = vv[u];
+                }
+            ++np;
         }
     }
-    return acc;
+    if (np > 0 && ok) az += drain_values<T, kVPend>(z, pj, pv, (1u << np) - 1u, st, tmo, row, ok);
 }
 
 // out[e] = sign * sum_c coef(c) * vec[cols[e] * k + c] for e in [e0, e1): the pattern-
@@ -409,7 +589,7 @@ __device__ __forceinline__ T finish_row(const ExecArgs &a, T num, T d) { return 
 // ---------------------------------------------------------------- item kinds
 // SpTRSV row (Table 2, forward substitution): x_i = (b_i - sum_{j<i} L_ij x_j) / L_ii.
 // `x` is both the output and the buffer the dependences are read from.
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ bool item_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask, T *x) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
@@ -421,7 +601,7 @@ __device__ bool item_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, un
         const bool act = c < k;
         // operands that need no wait are loaded before it, off the dependence chain
         const T bc = (s == 0 && act) ? __ldg(b + (size_t)row * k + c) : T(0);
-        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Lci, nullptr, Lv, rs + s, dg, S, x, k, c, act, a.flags,
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.Lci, nullptr, Lv, rs + s, dg, S, x, k, c, act, a.flags,
                                                          epoch, a.st, a.timeout_ns, row, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
         if (s == 0 && act) store_out<VF>(x + (size_t)row * k + c, finish_row<T>(a, bc - acc, d));
@@ -434,7 +614,7 @@ __device__ bool item_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, un
 // SpMV row of the second kernel with F = pattern(M): y_i = sum_j M_ij x_j, each x_j
 // waited for (§2.2 "Dependency Matrix F": row i of F lists the first-kernel iterations
 // row i of the second kernel reads).
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ bool item_spmv_dep(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask, const T *x) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int rs = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1);
@@ -443,7 +623,7 @@ __device__ bool item_spmv_dep(const ExecArgs &a, int row, unsigned epoch, int gl
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Mci, nullptr, (const T *)a.Mv, rs + s, re, S, x, k, c,
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.Mci, nullptr, (const T *)a.Mv, rs + s, re, S, x, k, c,
                                                          act, a.flags, epoch, a.st, a.timeout_ns, row, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
         if (s == 0 && act) y[(size_t)row * k + c] = acc;
@@ -453,10 +633,33 @@ __device__ bool item_spmv_dep(const ExecArgs &a, int row, unsigned epoch, int gl
 
 // Paired SpMV -> SpTRSV row (combination 2, F = I): r_i = b_i - A_i x_in stays in
 // registers, then z_i = (r_i - sum_{j<i} L_ij z_j) / L_ii.
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ra = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1);
+    if constexpr (VF) {
+        if (a.Lv == nullptr) {
+            // shared storage (Table 2 combination 2 as one Gauss-Seidel half-sweep): L = tril(A) is
+            // read from A's row, which is streamed once for both r_i and the solve
+            const int dp = __ldg(a.a_diag + row);
+            const T *Av = (const T *)a.Mv, *b = (const T *)a.b;
+            T *z = (T *)a.y;
+            const T d = load_diag<T>(a, Av, dp, row, gl);
+            bool ok = true;
+            for (int c0 = 0; c0 < k; c0 += kt) {
+                const int c = c0 + cl;
+                const bool act = c < k;
+                const T bc = (s == 0 && act) ? __ldg(b + (size_t)row * k + c) : T(0);
+                T ax, az;
+                gs_row_dot<T, VU>(a.Mci, Av, ra + s, dp, re, S, (const T *)a.xin, z, k, c, act, a.st, a.timeout_ns, row,
+                              ok, ax, az);
+                ax = slice_sum<LPR>(ax, kt, gmask);
+                az = slice_sum<LPR>(az, kt, gmask);
+                if (s == 0 && act) put_value(z + (size_t)row * k + c, finish_row<T>(a, (bc - ax) - az, d));
+            }
+            return group_ok<LPR>(ok, gmask);
+        }
+    }
     const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
     const T *Lv = (const T *)a.Lv, *b = (const T *)a.b;
     T *z = (T *)a.y;
@@ -470,7 +673,7 @@ __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int g
                                            act, a.flags, epoch, a.st, a.timeout_ns, row, ok);
         accA = slice_sum<LPR>(accA, kt, gmask);
         const T r = bc - accA;   // r_i is complete before the wait on z
-        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.Lci, nullptr, Lv, rs + s, dg, S, z, k, c, act, a.flags,
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.Lci, nullptr, Lv, rs + s, dg, S, z, k, c, act, a.flags,
                                                           epoch, a.st, a.timeout_ns, row, ok);
         accL = slice_sum<LPR>(accL, kt, gmask);
         if (s == 0 && act) store_out<VF>(z + (size_t)row * k + c, finish_row<T>(a, r - accL, d));
@@ -518,7 +721,7 @@ __device__ __forceinline__ T ic0_row_search(const ExecArgs &a, int rs, int dg, i
 // table the rows publish with their factor (a.ic0_rinv), so an entry costs one multiply. The
 // first chunk's pattern and A values (j0, q0, q1, av0) were loaded before the wait. Returns
 // sum_{k<i} L_ik^2 on every lane; the sum runs over the lanes that hold entries only.
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ __forceinline__ T ic0_row_pairs(const ExecArgs &a, int row, int rs, int dg, int gl, unsigned gmask, int j0,
                                            int q0, int q1, T av0, bool &ok) {
     const T *Av = (const T *)a.Lv;
@@ -681,7 +884,7 @@ __device__ bool item_ic0(const ExecArgs &a, int row, unsigned epoch, int gl, uns
 // j of L): u_j = (M^T gy)_j needs no wait; lam_j = (u_j - sum_{i>j} L_ij lam_i) / L_jj
 // waits for lam_i; gb = lam. Values of M^T and L^T come in transposed order (a.MTv, a.LTv);
 // the value gradients run afterwards as a separate streaming pass.
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ bool item_adj_trsv_spmv(const ExecArgs &a, int j, unsigned epoch, int gl, int gbase, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ms = __ldg(a.MTrp + j), me = __ldg(a.MTrp + j + 1);
@@ -696,7 +899,7 @@ __device__ bool item_adj_trsv_spmv(const ExecArgs &a, int j, unsigned epoch, int
         T u = row_dot<T, D_NONE, false>(a.MTci, nullptr, (const T *)a.MTv, ms + s, me, S, gy, k, c, act, a.flags,
                                         epoch, a.st, a.timeout_ns, j, ok);
         u = slice_sum<LPR>(u, kt, gmask);   // u_j is complete before the wait on lam
-        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
                                                           a.flags, epoch, a.st, a.timeout_ns, j, ok);
         accL = slice_sum<LPR>(accL, kt, gmask);
         if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, finish_row<T>(a, u - accL, d));
@@ -707,7 +910,7 @@ __device__ bool item_adj_trsv_spmv(const ExecArgs &a, int j, unsigned epoch, int
 }
 
 // Adjoint of SpMV -> SpTRSV, tag 0: lam_j = (gz_j - sum_{i>j} L_ij lam_i) / L_jj, gb = lam.
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ bool item_adj_lam(const ExecArgs &a, int j, unsigned epoch, int gl, int gbase, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ls = __ldg(a.LTrp + j), le = __ldg(a.LTrp + j + 1);
@@ -719,7 +922,7 @@ __device__ bool item_adj_lam(const ExecArgs &a, int j, unsigned epoch, int gl, i
         const int c = c0 + cl;
         const bool act = c < k;
         const T gc = (s == 0 && act) ? __ldg(gz + (size_t)j * k + c) : T(0);
-        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
+        T accL = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.LTci, nullptr, LTv, ls + 1 + s, le, S, lam, k, c, act,
                                                           a.flags, epoch, a.st, a.timeout_ns, j, ok);
         accL = slice_sum<LPR>(accL, kt, gmask);
         if (s == 0 && act) store_out<VF>(lam + (size_t)j * k + c, finish_row<T>(a, gc - accL, d));
@@ -730,7 +933,7 @@ __device__ bool item_adj_lam(const ExecArgs &a, int j, unsigned epoch, int gl, i
 }
 
 // Adjoint of SpMV -> SpTRSV, tag 1: gx_j = -sum_i A_ij lam_i, waiting for each lam_i.
-template <typename T, int LPR, bool VF>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
 __device__ bool item_adj_gx(const ExecArgs &a, int j, unsigned epoch, int gl, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ms = __ldg(a.MTrp + j), me = __ldg(a.MTrp + j + 1);
@@ -739,7 +942,7 @@ __device__ bool item_adj_gx(const ExecArgs &a, int j, unsigned epoch, int gl, un
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
-        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false>(a.MTci, nullptr, (const T *)a.MTv, ms + s, me, S,
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.MTci, nullptr, (const T *)a.MTv, ms + s, me, S,
                                                          (const T *)a.gb, k, c, act, a.flags, epoch, a.st,
                                                          a.timeout_ns, j, ok);
         acc = slice_sum<LPR>(acc, kt, gmask);
@@ -748,36 +951,136 @@ __device__ bool item_adj_gx(const ExecArgs &a, int j, unsigned epoch, int gl, un
     return group_ok<LPR>(ok, gmask);
 }
 
+// Paired SpTRSV -> SpTRSV row (Table 2 combination 1, F = I, same L): x_i = (b_i - sum_{j<i}
+// L_ij x_j) / L_ii, then z_i = (x_i - sum_{j<i} L_ij z_j) / L_ii while x_i is still in registers
+// (the row of L is read twice by the same lanes, the second time from L1). x goes to a.xs,
+// z to a.y; with value flags each is published by its store.
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
+__device__ bool item_trsv_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
+    const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
+    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+    const T *Lv = (const T *)a.Lv, *b = (const T *)a.b;
+    T *x = (T *)a.xs, *z = (T *)a.y;
+    const T d = load_diag<T>(a, Lv, dg, row, gl);
+    bool ok = true;
+    for (int c0 = 0; c0 < k; c0 += kt) {
+        const int c = c0 + cl;
+        const bool act = c < k;
+        const T bc = act ? __ldg(b + (size_t)row * k + c) : T(0);
+        T acc = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.Lci, nullptr, Lv, rs + s, dg, S, x, k, c, act, a.flags,
+                                                         epoch, a.st, a.timeout_ns, row, ok);
+        acc = slice_sum<LPR>(acc, kt, gmask);
+        const T xi = finish_row<T>(a, bc - acc, d);
+        if (s == 0 && act) store_out<VF>(x + (size_t)row * k + c, xi);
+        T acc2 = row_dot<T, VF ? D_VALUE : D_FLAG, false, VU>(a.Lci, nullptr, Lv, rs + s, dg, S, z, k, c, act, a.flags,
+                                                          epoch, a.st, a.timeout_ns, row, ok);
+        acc2 = slice_sum<LPR>(acc2, kt, gmask);
+        if (s == 0 && act) store_out<VF>(z + (size_t)row * k + c, finish_row<T>(a, xi - acc2, d));
+    }
+    ok = group_ok<LPR>(ok, gmask);
+    if (!VF) publish(a, row, epoch, gl, gmask, ok);
+    return ok;
+}
+
+// Paired SpILU0 -> SpTRSV row (Table 2 combination 6, F = I), whole warp, value flags only.
+// Zero fill-in ILU0 in its row-oriented (IKJ) form on A's pattern: row i's working copy w sits
+// in shared memory (lane l owns the entries t = l, l + 32, ...); for each k < i in the row,
+// ascending: l_ik = w_ik / u_kk, then every later entry w_ij with (k, j) in row k's pattern
+// loses l_ik u_kj (the lane owning j finds it by binary search in row k after its diagonal).
+// u_kk and u_kj are the values row k stored (each its own flag). The finished row is stored to
+// the factor (a.xs, on A's pattern: strictly lower part of the unit lower L, then U), and the
+// solve row with the unit lower factor follows from shared memory:
+// y_i = b_i - sum_{k<i} l_ik y_k. A zero pivot u_kk records SF_ERR_BREAKDOWN with row k.
+template <typename T>
+__device__ bool item_ilu0(const ExecArgs &a, int row, int gl) {
+    __shared__ T wbuf[kExecThreads / 32][kIluMaxRow];
+    T *w = wbuf[threadIdx.x >> 5];
+    const unsigned full = 0xffffffffu;
+    const int ra = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1), dp = __ldg(a.a_diag + row);
+    const int len = re - ra;
+    const T *Av = (const T *)a.Mv;
+    T *lu = (T *)a.xs;
+    bool ok = true;
+    for (int t = gl; t < len; t += 32) w[t] = __ldg(Av + ra + t);
+    __syncwarp(full);
+    for (int e = ra; e < dp; ++e) {
+        const int kr = __ldg(a.Mci + e);
+        const int dk = __ldg(a.a_diag + kr), kend = __ldg(a.Mrp + kr + 1);
+        T ukk = T(0);
+        if (gl == 0) ukk = poll_value(lu + dk, a.st, a.timeout_ns, row, ok);
+        ukk = __shfl_sync(full, ukk, 0);
+        if (__shfl_sync(full, ok ? 1 : 0, 0) == 0) {
+            ok = false;
+            break;
+        }
+        if (gl == 0 && ukk == T(0)) record_error(a.st, SF_ERR_BREAKDOWN, kr);
+        const T lik = w[e - ra] / ukk;
+        __syncwarp(full);
+        if (((e - ra) & 31) == gl) w[e - ra] = lik;
+        for (int t = gl; t < len; t += 32) {
+            const int f = ra + t;
+            if (f <= e) continue;
+            const int j = __ldg(a.Mci + f);
+            int lo = dk + 1, hi = kend;   // column j among row k's entries after its diagonal
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(a.Mci + mid) < j) lo = mid + 1; else hi = mid;
+            }
+            if (lo < kend && __ldg(a.Mci + lo) == j) w[t] -= lik * poll_value(lu + lo, a.st, a.timeout_ns, row, ok);
+        }
+        __syncwarp(full);
+    }
+    ok = !__any_sync(full, !ok);
+    for (int t = gl; t < len && ok; t += 32) put_value(lu + ra + t, w[t]);
+    const int kt = a.kt, S = 32 / kt, s = gl / kt, cl = gl % kt, k = a.k;
+    const T *b = (const T *)a.b;
+    T *y = (T *)a.y;
+    for (int c0 = 0; c0 < k && ok; c0 += kt) {
+        const int c = c0 + cl;
+        const bool act = c < k;
+        T acc = T(0);
+        if (act)
+            for (int e = ra + s; e < dp && ok; e += S)
+                acc += w[e - ra] * poll_value(y + (size_t)__ldg(a.Mci + e) * k + c, a.st, a.timeout_ns, row, ok);
+        acc = slice_sum<32>(acc, kt, full);
+        if (s == 0 && act && ok) put_value(y + (size_t)row * k + c, __ldg(b + (size_t)row * k + c) - acc);
+    }
+    return !__any_sync(full, !ok);
+}
+
 // Modes with value-flag launches (k = 1; IC0 modes for any k when the pair lists exist).
 constexpr bool mode_has_vf(int m) {
     return m == M_TRSV_SPMV || m == M_TRSV || m == M_SPMV_TRSV || m == M_ADJ_TRSV_SPMV || m == M_ADJ_SPMV_TRSV ||
-           m == M_IC0_TRSV || m == M_IC0;
+           m == M_IC0_TRSV || m == M_IC0 || m == M_TRSV_TRSV || m == M_ILU0_TRSV;
 }
 
-template <int MODE, typename T, int LPR, bool VF>
+template <int MODE, typename T, int LPR, bool VF, int VU>
 __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, unsigned epoch, int gl, int gbase,
                                          unsigned gmask) {
     if constexpr (MODE == M_TRSV_SPMV) {
-        if (tag == 0) return item_trsv<T, LPR, VF>(a, row, epoch, gl, gmask, (T *)a.xs);
-        return item_spmv_dep<T, LPR, VF>(a, row, epoch, gl, gmask, (const T *)a.xs);
+        if (tag == 0) return item_trsv<T, LPR, VF, VU>(a, row, epoch, gl, gmask, (T *)a.xs);
+        return item_spmv_dep<T, LPR, VF, VU>(a, row, epoch, gl, gmask, (const T *)a.xs);
     } else if constexpr (MODE == M_TRSV) {
-        return item_trsv<T, LPR, VF>(a, row, epoch, gl, gmask, (T *)a.y);
+        return item_trsv<T, LPR, VF, VU>(a, row, epoch, gl, gmask, (T *)a.y);
     } else if constexpr (MODE == M_SPMV_TRSV) {
-        return item_spmv_trsv<T, LPR, VF>(a, row, epoch, gl, gmask);
+        return item_spmv_trsv<T, LPR, VF, VU>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0_TRSV) {
         return item_ic0<T, LPR, true, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0) {
         return item_ic0<T, LPR, false, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_ADJ_TRSV_SPMV) {
-        return item_adj_trsv_spmv<T, LPR, VF>(a, row, epoch, gl, gbase, gmask);
+        return item_adj_trsv_spmv<T, LPR, VF, VU>(a, row, epoch, gl, gbase, gmask);
+    } else if constexpr (MODE == M_TRSV_TRSV) {
+        return item_trsv_trsv<T, LPR, VF, VU>(a, row, epoch, gl, gmask);
+    } else if constexpr (MODE == M_ILU0_TRSV) {
+        if constexpr (VF && LPR == 32) return item_ilu0<T>(a, row, gl);
+        else return false;   // not instantiated: ILU0 launches are whole-warp value-flag launches
     } else {
-        if (tag == 0) return item_adj_lam<T, LPR, VF>(a, row, epoch, gl, gbase, gmask);
+        if (tag == 0) return item_adj_lam<T, LPR, VF, VU>(a, row, epoch, gl, gbase, gmask);
         if (!a.gx) return true;    // gradient of x_in not requested
-        return item_adj_gx<T, LPR, VF>(a, row, epoch, gl, gmask);
+        return item_adj_gx<T, LPR, VF, VU>(a, row, epoch, gl, gmask);
     }
 }
-
-constexpr int kExecThreads = 256;
 
 // Resident blocks per SM the compiler budgets registers for: the default kernels keep all the
 // registers they want (latency-bound chains prefer fewer, faster threads); the occupancy
@@ -838,12 +1141,12 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
         if (LPR < TEAM && a.part_wide[p]) {
             // a long row: the whole team runs it (the cut gives it a partition of its own)
             const unsigned o = (unsigned)__ldg(a.order + q0);
-            if (ok) ok = run_item<MODE, T, TEAM, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl, tbase,
+            if (ok) ok = run_item<MODE, T, TEAM, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl, tbase,
                                                      tmask);
         } else {
             for (int q = q0 + grp; q < q1 && ok; q += G) {
                 const unsigned o = (unsigned)__ldg(a.order + q);
-                ok = run_item<MODE, T, LPR, VF>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
+                ok = run_item<MODE, T, LPR, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
             }
         }
         if (!__all_sync(tmask, ok)) break;

@@ -19,24 +19,32 @@ const void *block_kernel(int mode, int dtype, int lpr) {
 }  // namespace
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rdiag(int n, const int *__restrict__ Lrp, const T *__restrict__ Lv, T *vec,
-                                               T *__restrict__ rdiag, ExecState *st) {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)t;
-        vec[i] = unset_value<T>();
-        const T d = Lv[__ldg(Lrp + i + 1) - 1];
-        if (d == T(0)) record_error(st, SF_ERR_NONFINITE, i);
-        rdiag[i] = T(1) / d;
+__global__ void __launch_bounds__(256) k_rdiag(int n, int k, const int *__restrict__ Lrp, const T *__restrict__ Lv,
+                                               T *vec, T *__restrict__ rdiag, ExecState *st,
+                                               const int *__restrict__ diag_at, T *vec2) {
+    const long long nk = (long long)n * k;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nk; t += (long long)gridDim.x * blockDim.x) {
+        vec[t] = unset_value<T>();
+        if (vec2) vec2[t] = unset_value<T>();
+        if (t < n) {
+            const int i = (int)t;
+            const T d = Lv[diag_at ? __ldg(diag_at + i) : __ldg(Lrp + i + 1) - 1];
+            if (d == T(0)) record_error(st, SF_ERR_NONFINITE, i);
+            rdiag[i] = T(1) / d;
+        }
     }
 }
 
-cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void *vec, void *rdiag, ExecState *st,
-                         cudaStream_t s) {
-    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(((long long)n + 255) / 256, 65535LL));
+cudaError_t launch_rdiag(int dtype, int n, int k, const int *Lrp, const void *Lv, void *vec, void *rdiag,
+                         ExecState *st, cudaStream_t s, const int *diag_at, void *vec2) {
+    const long long nk = (long long)n * k;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((nk + 255) / 256, 65535LL));
     if (dtype == 0)
-        k_rdiag<double><<<grid, 256, 0, s>>>(n, Lrp, (const double *)Lv, (double *)vec, (double *)rdiag, st);
+        k_rdiag<double><<<grid, 256, 0, s>>>(n, k, Lrp, (const double *)Lv, (double *)vec, (double *)rdiag, st,
+                                             diag_at, (double *)vec2);
     else
-        k_rdiag<float><<<grid, 256, 0, s>>>(n, Lrp, (const float *)Lv, (float *)vec, (float *)rdiag, st);
+        k_rdiag<float><<<grid, 256, 0, s>>>(n, k, Lrp, (const float *)Lv, (float *)vec, (float *)rdiag, st, diag_at,
+                                            (float *)vec2);
     return cudaGetLastError();
 }
 

@@ -511,7 +511,9 @@ __global__ void k_encode_order(long long nv, int n1, const unsigned *__restrict_
 
 // c(v) of §3.1 (nonzeros touched by the iteration) + 1 (adjoint items exclude the value
 // gradients, which run as a separate streaming pass); formulas per `what`:
-// 0 SEP, 1 PAIRED_T, 2 SEP_T, 3 SpMV->SpTRSV, 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0.
+// 0 SEP, 1 PAIRED_T, 2 SEP_T, 3 SpMV->SpTRSV, 4 SpIC0->SpTRSV, 5 SpTRSV, 6 SpIC0,
+// 7 SpTRSV->SpTRSV (the row of L twice), 8 SpILU0->SpTRSV (row i of A, the rows of A it
+// eliminates with, and the solve row).
 __global__ void k_costs(int what, int n, const int *__restrict__ Lrp, const int *__restrict__ Lci,
                         const int *__restrict__ Mrp, const int *__restrict__ LTrp, const int *__restrict__ MTrp,
                         int *__restrict__ cost) {
@@ -527,6 +529,11 @@ __global__ void k_costs(int what, int n, const int *__restrict__ Lrp, const int 
             const int j = Lci[e];
             sj += Lrp[j + 1] - Lrp[j];
         }
+    if (what == 8)
+        for (int e = Lrp[i]; e < Lrp[i + 1] - 1; ++e) {
+            const int j = Lci[e];
+            sj += Mrp[j + 1] - Mrp[j];
+        }
     switch (what) {
         case 0: cost[i] = nl + 1; cost[n + i] = nm + 1; break;
         case 1: cost[i] = cm + cl + 1; break;
@@ -534,6 +541,8 @@ __global__ void k_costs(int what, int n, const int *__restrict__ Lrp, const int 
         case 3: cost[i] = nm + nl + 1; break;
         case 4: cost[i] = 2 * nl + sj + 1; break;
         case 5: cost[i] = nl + 1; break;
+        case 7: cost[i] = 2 * nl + 1; break;
+        case 8: cost[i] = nm + sj + nl + 1; break;
         default: cost[i] = nl + sj + 1; break;
     }
 }
@@ -889,6 +898,44 @@ cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci
     e = cudaMemcpyAsync(rp_out + total_rows, &last, sizeof(int), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(s);   // `last` and `h` live on this stack frame
+}
+
+// Diagonal positions of A's rows and a comparison of L with tril(A): a_diag[i] = position of
+// A_ii (or -1); bit 0 of *bad: a row of A misses its diagonal; bit 1: L's row differs from
+// the lower part of A's row (diagonal included).
+__global__ void k_tril_map(int n, const int *__restrict__ Arp, const int *__restrict__ Aci,
+                           const int *__restrict__ Lrp, const int *__restrict__ Lci, int *__restrict__ a_diag,
+                           unsigned *bad) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)t;
+        const int ra = Arp[i], re = Arp[i + 1];
+        int lo = ra, hi = re;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (Aci[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        const int dp = (lo < re && Aci[lo] == i) ? lo : -1;
+        a_diag[i] = dp;
+        if (dp < 0) {
+            atomicOr(bad, 1u);
+            continue;
+        }
+        const int ls = Lrp[i], le = Lrp[i + 1];
+        bool same = le - ls == dp - ra + 1;
+        for (int u = 0; same && u < le - ls; ++u) same = Lci[ls + u] == Aci[ra + u];
+        if (!same) atomicOr(bad, 2u);
+    }
+}
+
+cudaError_t tril_map(const DevCsr &A, const DevCsr &L, int *a_diag, unsigned *bad_host, cudaStream_t s, Arena &ar) {
+    unsigned *bad = (unsigned *)ar.alloc(sizeof(unsigned));
+    if (!bad) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_tril_map<<<grid_for(A.n_rows, 256), 256, 0, s>>>(A.n_rows, A.rowptr, A.colidx, L.rowptr, L.colidx, a_diag, bad);
+    e = cudaMemcpyAsync(bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
 }
 
 cudaError_t check_pattern(const DevCsr &m, int lower, unsigned long long *status_host, cudaStream_t s, Arena &ar) {

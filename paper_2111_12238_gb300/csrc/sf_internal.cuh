@@ -25,7 +25,9 @@ enum Mode {
     M_IC0 = 4,         // single kernel: IC0 row
     M_ADJ_TRSV_SPMV = 5,  // paired: u_j = (M^T gy)_j, lam_j = (u_j - (L^T lam)_j) / L_jj
     M_ADJ_SPMV_TRSV = 6,  // separated: lam_j (tag 0), gx_j = -(A^T lam)_j (tag 1)
-    M_COUNT = 7
+    M_TRSV_TRSV = 7,   // paired: x_i = (b_i - L_i x) / L_ii, then z_i = (x_i - L_i z) / L_ii
+    M_ILU0_TRSV = 8,   // paired: up-looking ILU0 row i of A, then the unit lower solve row i
+    M_COUNT = 9
 };
 
 // Per-direction launch state, one 32-byte block in device memory. `epoch` numbers the
@@ -87,6 +89,9 @@ struct ExecArgs {
     const int *ic0_pp;
     const int2 *ic0_pairs;
     void *ic0_rinv;                     // IC0: 1 / L_ii per row, written with the factor row
+    // position of the diagonal in every row of M (= A): ILU0 rows, and SpMV -> SpTRSV rows that
+    // read L = tril(A) from A's storage (shared storage, Lv == NULL); else NULL
+    const int *a_diag;
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)
@@ -117,10 +122,18 @@ cudaError_t launch_block_tma(int mode, int dtype, int blocks, int nc, cudaStream
                              cudaEvent_t ev_start, cudaEvent_t ev_stop);
 cudaError_t launch_block_ws(int mode, int dtype, int blocks, int nc, cudaStream_t s, const ExecArgs &a,
                             cudaEvent_t ev_start, cudaEvent_t ev_stop);
-// Pre-pass of partition launches with value flags: resets vec[0..n) to the all-ones pattern
+// Pre-pass of partition launches with value flags: resets vec[0..n*k) to the all-ones pattern
 // and writes rdiag[i] = 1 / L_ii (L's diagonal is the last entry of each row).
-cudaError_t launch_rdiag(int dtype, int n, const int *Lrp, const void *Lv, void *vec, void *rdiag, ExecState *st,
-                         cudaStream_t s);
+// The diagonal is Lv[diag_at[i]] instead when diag_at is given (L read from A's storage); vec2,
+// when given, is reset too (a second published vector).
+cudaError_t launch_rdiag(int dtype, int n, int k, const int *Lrp, const void *Lv, void *vec, void *rdiag,
+                         ExecState *st, cudaStream_t s, const int *diag_at = nullptr, void *vec2 = nullptr);
+// Table 2 combinations 1 (SpTRSV -> SpTRSV) and 6 (SpILU0 -> SpTRSV); ILU0 launches run whole-warp
+// rows with value flags only.
+cudaError_t launch_exec_next(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
+                             const ExecArgs &a);
+int occupancy_next(int mode, int dtype, int lpr, bool vf, int team, int minb);
+constexpr int kIluMaxRow = 256;   // longest row of A an ILU0 row keeps on chip
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team, int minb);
 cudaError_t launch_exec_trsv(int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,

@@ -19,7 +19,7 @@ import torch
 
 from . import _build
 
-PAIRS = {"trsv_spmv": 0, "ic0_trsv": 1, "spmv_trsv": 2, "trsv": 3, "ic0": 4}
+PAIRS = {"trsv_spmv": 0, "ic0_trsv": 1, "spmv_trsv": 2, "trsv": 3, "ic0": 4, "trsv_trsv": 5, "ilu0_trsv": 6}
 SF_WANT_ADJOINT = 0x1
 SF_EPOCH_FLAGS = 0x2
 SF_DYNAMIC_QUEUE = 0x4

@@ -188,9 +188,12 @@ class Gpu:
         self.tmp = torch.empty_like(self.b)
         self.tmp2 = torch.empty_like(self.b)
         self.stream = torch.cuda.current_stream()
+        self.shared = True
 
     def fwd(self):
-        self.sched.execute(self.Lv, self.Mv, b=self.b, x_in=self.x_in, y=self.y, x_save=self.xs)
+        # SpMV -> SpTRSV reads L = tril(A) from A's rows (shared storage) unless told otherwise
+        Lv = None if (self.pair == "spmv_trsv" and self.shared) else self.Lv
+        self.sched.execute(Lv, self.Mv, b=self.b, x_in=self.x_in, y=self.y, x_save=self.xs)
 
     def adj(self):
         s = self.sched
@@ -374,6 +377,9 @@ def run_gpu(args):
                        rhs_tile=kt if wl["k"] > 1 else 0, team_lanes=args.team, block_rows=args.block_rows,
                        exec_mode=args.exec_mode, g2_placement=args.g2)
     g = Gpu(wl, args.dtype, device, launch_opts)
+    if args.slices > 0:
+        g.sched.set_slices(-1, args.slices)
+        g.un_sched.set_slices(0, args.slices)
     if wl["adj"] and args.adj_exec_mode >= 0:
         g.sched.reblock(1, args.adj_block_rows, args.adj_exec_mode, 0)
     fns = [g.fwd] + ([g.adj] if wl["adj"] else [])
@@ -639,6 +645,7 @@ def main():
                     help="placement of second-kernel rows: 0 earliest wavefront, -1 last, d > 0 delayed by d")
     ap.add_argument("--adj-exec-mode", type=int, default=-1, help="executor of the adjoint pass (-1: as --exec-mode)")
     ap.add_argument("--adj-block-rows", type=int, default=0, help="rows per block of the adjoint's row blocks")
+    ap.add_argument("--slices", type=int, default=0, help="split rows costlier than this over several teams (0: off)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the default launch shape)")
     ap.add_argument("--tune-seconds", type=float, default=8.0, help="time budget of each autotuning search")
     args = ap.parse_args()

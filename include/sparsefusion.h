@@ -241,6 +241,10 @@ typedef struct {
     int64_t ic0_pairs;                 /* IC0 schedules: intersection pairs listed by the
                                           inspector (-1: too many, not listed); else 0 */
     int32_t ic0_use_pairs, reserved3;  /* 1 when the factor reads the listed pairs */
+    int64_t slice_cost, adj_slice_cost;   /* see sf_schedule_set_slices (0: off) */
+    int32_t slice_units, adj_slice_units; /* queue units with split rows (0: no row split) */
+    int32_t max_slices, adj_max_slices;   /* most slices of one row */
+    int32_t fwd_rhs_tile, adj_rhs_tile;   /* right-hand-side tile of each direction (0: automatic) */
 } sf_info;
 sf_status sf_schedule_query(const sf_schedule *sch, sf_info *info);
 
@@ -326,6 +330,26 @@ sf_status sf_schedule_set_ic0_pairs(sf_schedule *sch, int32_t use);
  * 0 (the default) runs one class. Applies to the forward (0), adjoint (1) or both (-1)
  * schedules; paired schedules ignore it. No GPU work. */
 sf_status sf_schedule_set_split(sf_schedule *sch, int32_t which, int32_t class0_pct);
+
+/* Execution-time split of long rows (§3.1 vertex cost c(v) used to balance the load of the
+ * executor, not only of partitions): in the forward (which = 0), adjoint (1) or both (-1)
+ * schedules, every partition holding a single SpTRSV row, SpMV -> SpTRSV row or transposed
+ * solve row (adjoints) whose cost exceeds cost_per_slice is run as m = ceil(cost /
+ * cost_per_slice) slices (at most 32) by m teams: each slice streams a contiguous chunk of the
+ * row's entries as their inputs arrive, m - 1 helpers store partial sums (library scratch of
+ * m - 1 values per right-hand side, published by value), the owner slice (queued after its
+ * helpers) adds them in slice order and finishes the row. Levels, order and partitions are
+ * unchanged. Applies to launches that publish through values (k = 1, or 16 or more lanes per
+ * row) of the partition executor; other launches run rows whole. 0 turns it off (default).
+ * Synchronises `stream`; no launch of this schedule may be pending on another stream. */
+sf_status sf_schedule_set_slices(sf_schedule *sch, int32_t which, int64_t cost_per_slice, void *stream);
+
+/* Right-hand-side tile of the forward (0), adjoint (1) or both (-1) schedules: the columns of
+ * the k right-hand sides that the lanes of a row handle side by side (a power of two up to
+ * 32; rows then get at least that many lanes); 0 returns to the schedule's tile (the
+ * rhs_tile option or sf_schedule_set_launch; automatic when that is 0, the power of two at or
+ * above k, at most 32). Chosen per direction by the autotuner. No GPU work. */
+sf_status sf_schedule_set_rhs_tile(sf_schedule *sch, int32_t which, int32_t rhs_tile);
 
 /* Copies a row-block schedule to HOST buffers: order[n_items] (row | kernel << 31, sorted
  * by (block, level, kernel, row)), block_ptr[n_blocks+1], seg_ptr[block_segments+1] (first

@@ -7,7 +7,10 @@ cp.async or with packed records and bulk copies, and the plain one) with several
 per partition), then, for separated schedules, the best shape with the second kernel's
 vertices placed later (``sf_schedule_replace``), the best partition shape on the executor's
 occupancy variants (``sf_schedule_set_occupancy``) and with the teams split between the two
-partition classes (``sf_schedule_set_split``). Candidates are applied without re-inspecting: ``sf_schedule_reblock``
+partition classes (``sf_schedule_set_split``), for several right-hand sides with other
+right-hand-side tiles (``sf_schedule_set_rhs_tile``), and with long rows split over several
+teams at several costs per slice (``sf_schedule_set_slices``). Candidates are applied without
+re-inspecting: ``sf_schedule_reblock``
 rebuilds the row-block order, ``sf_schedule_recut`` re-cuts the partitions for a new cost
 target (items per partition x mean vertex cost); levels are kept.
 Results are cached in a JSON file (``SF_TUNE_CACHE``, default
@@ -31,6 +34,8 @@ DEFAULT_BLOCK_ROWS = (1024, 2048, 4096, 8192, 16384)
 DEFAULT_BLOCK_LANES = (1, 2, 4, 32)
 DEFAULT_SPLITS = (50, 65, 80, 90)
 DEFAULT_PLACEMENTS = (-1, 2, 8, 32)
+DEFAULT_RHS_TILES = (1, 2, 4, 8, 16, 32)
+DEFAULT_SLICES = (32, 64, 128, 256, 512)
 
 
 def _cache_path() -> str:
@@ -87,6 +92,8 @@ def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     """Applies one candidate launch shape to direction `which` of the schedule."""
     sched.replace(which, c.get("g2", 0))   # no-op unless the placement changes
     sched.set_occupancy(which, c.get("occ", 1))
+    sched.set_rhs_tile(which, c.get("rt", 0))
+    sched.set_slices(which, c.get("slices", 0) if c["exec"] == "partitions" else 0)
     if c["exec"] == "blocks":
         sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
         sched.set_split(which, 0)
@@ -105,6 +112,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
          teams: Sequence[int] = DEFAULT_TEAMS, blocks: bool = True,
          block_rows: Sequence[int] = DEFAULT_BLOCK_ROWS, block_lanes: Sequence[int] = DEFAULT_BLOCK_LANES,
          splits: Sequence[int] = DEFAULT_SPLITS, placements: Sequence[int] = DEFAULT_PLACEMENTS, occupancy=True,
+         rhs_tiles: Sequence[int] = DEFAULT_RHS_TILES, slices: Sequence[int] = DEFAULT_SLICES,
          reps: int = 3, budget_s: float = 20.0,
          use_cache: bool = True) -> Dict:
     """Chooses the executor and its launch shape for `which` (0 forward, 1 adjoint) of
@@ -193,9 +201,41 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
         trials.append(dict(c, ms=ms))
         if ms < best["ms"]:
             best = trials[-1]
+    # several right-hand sides: the best partition shape with the other right-hand-side tiles
+    # (lanes at least the tile; 16 or more lanes publish rows through their values)
+    if best is not None and best["exec"] == "partitions" and k > 1 and rhs_tiles:
+        base = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "occ")}
+        for rt in rhs_tiles:
+            if rt == kt or rt > 32:
+                continue
+            for L in sorted({max(base["lanes"], rt), 32}):
+                c = dict(base, rt=rt, lanes=L, team=max(base["team"], L))
+                if c["items"] > max(1, c["team"] // L) * 4:
+                    c["items"] = max(1, c["team"] // L)
+                _apply(sched, which, c, mean)
+                ms = _time(run, reps)
+                sched.check()
+                trials.append(dict(c, ms=ms))
+                if ms < best["ms"]:
+                    best = trials[-1]
+    # long rows split over several teams at several costs per slice
+    if best is not None and best["exec"] == "partitions" and slices:
+        base = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "occ", "rt")}
+        for sc in slices:
+            c = dict(base, slices=sc)
+            _apply(sched, which, c, mean)
+            inf2 = sched.info()
+            if (inf2["slice_units"] if which == 0 else inf2["adj_slice_units"]) == 0:
+                continue   # nothing to split at this cost (or a kind that is not split)
+            ms = _time(run, reps)
+            sched.check()
+            trials.append(dict(c, ms=ms))
+            if ms < best["ms"]:
+                best = trials[-1]
     if best is not None and best["exec"] == "partitions" and splits and separated:
         for pct in splits:
-            c = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "occ")}
+            c = {kk: v for kk, v in best.items()
+                 if kk in ("exec", "lanes", "items", "team", "g2", "occ", "rt", "slices")}
             c["split"] = pct
             _apply(sched, which, c, mean)
             ms = _time(run, reps)

@@ -91,6 +91,12 @@ struct Dir {
     int nvp = 0, packed_B = 0;
     unsigned *flags = nullptr;
     ExecState *st = nullptr;
+    // long rows split at execution time (sf_schedule_set_slices): queue units, partial slots
+    long long slice_cost = 0;   // cost per slice (0: off)
+    int kt = 0;                 // right-hand-side tile of this direction (0: the schedule's)
+    int4 *xlist = nullptr;      // owned (cudaMalloc), rebuilt with every cut
+    int nx = 0, max_m = 1;
+    long long n_slots = 0;
 };
 
 const ExecState kInitState = {0u, 0u, 1u, 0u, 0u, 0, 0u, 0u};
@@ -153,6 +159,8 @@ struct sf_schedule {
     std::mutex mu;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    void *scratch2 = nullptr;   // partial sums of split rows
+    size_t scratch2_bytes = 0;
     int device = 0;
     int sms = 1;
 };
@@ -204,6 +212,57 @@ sf_status copy_pattern(sf_schedule *S, const sf_csr *src, DevCsr &dst, cudaStrea
     return SF_OK;
 }
 
+// Execution-time split of long rows (one direction): every partition holding a single vertex
+// of cost above d.slice_cost whose kind the executor can split (SpTRSV rows, SpMV -> SpTRSV
+// rows, the transposed solve rows of the adjoints) becomes m = ceil(cost / slice_cost) <= 32
+// queue units, its helpers first and its owner last; other partitions stay one unit each.
+// The units and partial-sum slots go to d.xlist / d.n_slots; nothing to split clears them.
+sf_status slice_dir(sf_schedule *S, Dir &d) {
+    if (d.xlist) {
+        cudaFree(d.xlist);
+        d.xlist = nullptr;
+    }
+    d.nx = 0;
+    d.n_slots = 0;
+    d.max_m = 1;
+    if (d.slice_cost <= 0) return SF_OK;
+    const bool fwd_ok = S->pair == SF_TRSV || S->pair == SF_SPMV_TRSV || S->pair == SF_TRSV_SPMV;
+    const bool ok_kind = (&d == &S->adj) ? true : fwd_ok;
+    if (!ok_kind) return SF_OK;
+    const int P = d.n_parts;
+    std::vector<int> pp((size_t)P + 1), order((size_t)d.nv), cost((size_t)d.nv);
+    SF_CK(cudaMemcpy(pp.data(), d.part_ptr, sizeof(int) * pp.size(), cudaMemcpyDeviceToHost), "slices");
+    SF_CK(cudaMemcpy(order.data(), d.order, sizeof(int) * order.size(), cudaMemcpyDeviceToHost), "slices");
+    SF_CK(cudaMemcpy(cost.data(), d.cost, sizeof(int) * cost.size(), cudaMemcpyDeviceToHost), "slices");
+    std::vector<int4> xl;
+    xl.reserve((size_t)P);
+    long long slot = 0;
+    for (int p = 0; p < P; ++p) {
+        int m = 1;
+        if (pp[p + 1] - pp[p] == 1) {
+            const unsigned o = (unsigned)order[pp[p]];
+            const int tag = (int)(o >> 31), row = (int)(o & 0x7fffffffu);
+            const long long c = cost[(size_t)tag * S->n + row];
+            if (tag == 0 && c > d.slice_cost) m = (int)std::min<long long>(32, (c + d.slice_cost - 1) / d.slice_cost);
+        }
+        if (m > 1) {
+            if (slot + m > (1LL << 30)) return fail(SF_ERR_UNSUPPORTED, "too many row slices");
+            for (int sl = 0; sl < m; ++sl) xl.push_back(make_int4(p, sl, m, (int)slot));
+            slot += m - 1;
+            d.max_m = std::max(d.max_m, m);
+        } else {
+            xl.push_back(make_int4(p, 0, 1, 0));
+        }
+    }
+    if (slot == 0) return SF_OK;
+    if (xl.size() >= (size_t)(1LL << 31)) return fail(SF_ERR_UNSUPPORTED, "too many queue units");
+    SF_CK(cudaMalloc(&d.xlist, sizeof(int4) * xl.size()), "slices");
+    SF_CK(cudaMemcpy(d.xlist, xl.data(), sizeof(int4) * xl.size(), cudaMemcpyHostToDevice), "slices");
+    d.nx = (int)xl.size();
+    d.n_slots = slot;
+    return SF_OK;
+}
+
 // Cost prefix and partition cut of one direction (the part of the inspection that the
 // launch shape influences): C_user > 0 is the cost target, else about one round of a
 // team's groups (at most eight items).
@@ -234,7 +293,7 @@ sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Aren
         e = split_partition_classes(d.n_parts, d.part_ptr, d.order, d.plist, &d.n_parts0, s, tmp);
         if (e != cudaSuccess) return from_cuda(e, "partition classes");
     }
-    return SF_OK;
+    return slice_dir(S, d);
 }
 
 // Row-block order of one direction for blocks of B rows (0: automatic, 8192 rows or n).
@@ -478,11 +537,13 @@ sf_schedule *new_schedule(sf_pair pair) {
     return S;
 }
 
-sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void **out) {
+sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void **out, int which = 0) {
     sf_schedule *S = const_cast<sf_schedule *>(Sc);
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->scratch_bytes >= bytes) {
-        *out = S->scratch;
+    void *&buf = which ? S->scratch2 : S->scratch;
+    size_t &have = which ? S->scratch2_bytes : S->scratch_bytes;
+    if (have >= bytes) {
+        *out = buf;
         return SF_OK;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -490,14 +551,14 @@ sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void 
     if (cs != cudaStreamCaptureStatusNone)
         return fail(SF_ERR_INVALID_ARG, "this call needs a library-owned buffer that is allocated on first use; "
                                         "make one such call before capturing the stream");
-    if (S->scratch) {
-        cudaFree(S->scratch);
-        S->scratch = nullptr;
-        S->scratch_bytes = 0;
+    if (buf) {
+        cudaFree(buf);
+        buf = nullptr;
+        have = 0;
     }
-    SF_CK(cudaMalloc(&S->scratch, bytes), "scratch allocation");
-    S->scratch_bytes = bytes;
-    *out = S->scratch;
+    SF_CK(cudaMalloc(&buf, bytes), "scratch allocation");
+    have = bytes;
+    *out = buf;
     return SF_OK;
 }
 
@@ -532,7 +593,8 @@ void *value_flag_buffer(int mode, const ExecArgs &a) {
 }
 
 sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int k, ExecArgs &a, cudaStream_t s) {
-    const int kt = S->kt ? std::min(S->kt, 32) : std::min(pow2_ceil(k), 32);
+    const int kt_s = d.kt ? d.kt : S->kt;
+    const int kt = kt_s ? std::min(kt_s, 32) : std::min(pow2_ceil(k), 32);
     const int lpr = std::max(d.lpr, kt);
     const int team = lpr <= 8 ? d.team : 32;
     a.order = d.order;
@@ -671,6 +733,10 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
                            shared ? S->a_diag : nullptr, mode == M_TRSV_TRSV ? a.y : nullptr),
               "value-flag reset");
     }
+    // long rows split over several teams (value flags; the kinds slice_dir selected)
+    const bool sliced = vf && d.nx > 0 &&
+                        (mode == M_TRSV || mode == M_TRSV_SPMV || mode == M_SPMV_TRSV || mode == M_ADJ_SPMV_TRSV ||
+                         mode == M_ADJ_TRSV_SPMV);
     const int minb = d.minb;
     const int lpr_l = ilu0 ? 32 : lpr, team_l = ilu0 ? 32 : team;
     const bool vf_l = ilu0 ? true : vf;
@@ -678,14 +744,28 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     if (S->blocks_per_sm > 0) per_sm = std::min(per_sm, S->blocks_per_sm);
     long long blocks = (long long)per_sm * S->sms;
     const long long teams_per_block = 8LL * (32 / team_l);
-    blocks = std::min<long long>(blocks, ((long long)d.n_parts + teams_per_block - 1) / teams_per_block);
+    const long long units = sliced ? d.nx : d.n_parts;
+    blocks = std::min<long long>(blocks, (units + teams_per_block - 1) / teams_per_block);
     blocks = std::max<long long>(blocks, 1);
+    a.xlist = nullptr;
+    a.nx = 0;
+    a.parts = nullptr;
+    if (sliced && blocks * teams_per_block >= d.max_m) {
+        // the helpers' partial sums start as the all-ones pattern
+        const size_t es = dt == SF_F64 ? 8 : 4;
+        const size_t bytes = es * (size_t)d.n_slots * (size_t)k;
+        sf_status st = get_scratch(S, bytes, s, &a.parts, 1);
+        if (st != SF_OK) return st;
+        SF_CK(cudaMemsetAsync(a.parts, 0xff, bytes, s), "value-flag reset");
+        a.xlist = d.xlist;
+        a.nx = d.nx;
+    }
     // two partition classes when a split is set: split_pct percent of the teams run the
     // partitions that open with a first-kernel row, the others the second-kernel ones
     const long long nteams = blocks * teams_per_block;
     a.plist = nullptr;
     if (d.split_pct > 0 && d.plist && d.n_parts0 > 0 && d.n_parts0 < d.n_parts && nteams >= 2 &&
-        !S->dynamic_queue) {
+        !S->dynamic_queue && !a.xlist) {
         a.plist = d.plist;
         a.n_parts0 = d.n_parts0;
         const long long t0 = (nteams * d.split_pct + 50) / 100;
@@ -1070,6 +1150,14 @@ SF_API sf_status sf_schedule_query(const sf_schedule *S, sf_info *info) {
     info->adj_min_blocks = S->adj.minb;
     info->ic0_pairs = (S->pair == SF_IC0_TRSV || S->pair == SF_IC0) ? (S->ic0_pp ? S->ic0_npairs : -1) : 0;
     info->ic0_use_pairs = (S->ic0_pp && S->ic0_use_pairs) ? 1 : 0;
+    info->slice_cost = S->fwd.slice_cost;
+    info->adj_slice_cost = S->adj.slice_cost;
+    info->slice_units = S->fwd.nx;
+    info->adj_slice_units = S->adj.nx;
+    info->max_slices = S->fwd.max_m;
+    info->adj_max_slices = S->adj.max_m;
+    info->fwd_rhs_tile = S->fwd.kt ? S->fwd.kt : S->kt;
+    info->adj_rhs_tile = S->adj.kt ? S->adj.kt : S->kt;
     info->block_segments = S->fwd.n_segs;
     info->adj_block_segments = S->adj.n_segs;
     info->block_threads = S->fwd.present ? block_threads(S->fwd) : 0;
@@ -1212,7 +1300,8 @@ SF_API sf_status sf_schedule_launches(const sf_schedule *S, int32_t which, int32
                          S->pair == SF_TRSV_TRSV;
     // the same choice as launch(): values publish rows for k = 1, or for any k with 16 or more
     // lanes per row
-    const int kt = S->kt ? std::min(S->kt, 32) : std::min(pow2_ceil(k), 32);
+    const int kt_s = d.kt ? d.kt : S->kt;
+    const int kt = kt_s ? std::min(kt_s, 32) : std::min(pow2_ceil(k), 32);
     const int lpr = std::max(d.lpr, kt);
     const bool vf = !S->epoch_flags && vf_pair && (long long)S->n * k <= 0x7fffffffLL && (k == 1 || lpr >= 16);
     int n = 0;
@@ -1265,6 +1354,34 @@ SF_API sf_status sf_schedule_set_split(sf_schedule *S, int32_t which, int32_t cl
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w)
         if ((which == -1 || which == w) && dirs[w]->present) dirs[w]->split_pct = class0_pct;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_rhs_tile(sf_schedule *S, int32_t which, int32_t rhs_tile) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (rhs_tile != 0 && !is_pow2_upto32(rhs_tile))
+        return fail(SF_ERR_INVALID_ARG, "rhs_tile must be 0 or a power of two in [1, 32]");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w)
+        if ((which == -1 || which == w) && dirs[w]->present) dirs[w]->kt = rhs_tile;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_slices(sf_schedule *S, int32_t which, int64_t cost_per_slice, void *stream) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
+    if (cost_per_slice < 0) return fail(SF_ERR_INVALID_ARG, "cost_per_slice must be >= 0");
+    if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
+    SF_CK(cudaStreamSynchronize((cudaStream_t)stream), "slices");
+    Dir *dirs[2] = {&S->fwd, &S->adj};
+    for (int w = 0; w < 2; ++w) {
+        if ((which != -1 && which != w) || !dirs[w]->present) continue;
+        dirs[w]->slice_cost = cost_per_slice;
+        sf_status st = slice_dir(S, *dirs[w]);
+        if (st != SF_OK) return st;
+    }
     return SF_OK;
 }
 
@@ -1321,6 +1438,9 @@ SF_API sf_status sf_schedule_debug_swap(sf_schedule *S, int64_t q1, int64_t q2) 
 SF_API void sf_schedule_destroy(sf_schedule *S) {
     if (!S) return;
     if (S->scratch) cudaFree(S->scratch);
+    if (S->scratch2) cudaFree(S->scratch2);
+    if (S->fwd.xlist) cudaFree(S->fwd.xlist);
+    if (S->adj.xlist) cudaFree(S->adj.xlist);
     delete S;
 }
 

@@ -1048,6 +1048,129 @@ __device__ bool item_ilu0(const ExecArgs &a, int row, int gl) {
     return !__any_sync(full, !ok);
 }
 
+// Chunk s of m equal chunks of the entry range [e0, e1).
+__device__ __forceinline__ void slice_range(int e0, int e1, int s, int m, int &lo, int &hi) {
+    const int chunk = (e1 - e0 + m - 1) / m;
+    lo = min(e1, e0 + s * chunk);
+    hi = min(e1, lo + chunk);
+}
+
+// One slice of a long row split at execution time (whole team, value flags). The row's dot
+// products are cut into m chunks of entries; slices 0 .. m-2 (the helpers, earlier in the
+// queue) each add up their chunk and store the partial sums (one per right-hand-side column)
+// to a.parts[(slot + s) * k + c], every value its own flag; slice m-1 (the owner, queued after
+// its helpers) adds up the last chunk, whose inputs arrive last, waits for the helpers'
+// partials, sums them in slice order and finishes the row exactly as the item does. Several
+// teams thus stream one long row as its inputs arrive. Kinds: SpTRSV rows (SpTRSV -> SpMV
+// tag 0, SpTRSV alone), SpMV -> SpTRSV rows (A and L parts, or A's row in shared storage) and
+// the transposed solve rows of the adjoints.
+template <int MODE, typename T, int LPR, int VU>
+__device__ bool run_slice(const ExecArgs &a, int tag, int row, int s, int m, int slot, int gl, unsigned gmask) {
+    const int kt = a.kt, S = LPR / kt, ls = gl / kt, cl = gl % kt, k = a.k;
+    const bool owner = s == m - 1;
+    T *parts = (T *)a.parts;
+    bool ok = true;
+    int lo, hi, lo2 = 0, hi2 = 0;
+    const T *vals = nullptr, *vals2 = nullptr;
+    const int *cols = nullptr, *cols2 = nullptr;
+    const T *vec = nullptr;       // the vector the waited-for part reads
+    const T *vec2 = nullptr;      // the vector of the part that waits for nothing
+    T *out = nullptr;
+    T d = T(0);
+    int dp = -1;                  // shared storage: diagonal position of A's row
+    const T *first = nullptr;     // owner: b, gz (added) or NULL
+    T sign2 = T(1);               // sign of the part that waits for nothing in p
+    if constexpr (MODE == M_TRSV || MODE == M_TRSV_SPMV) {
+        const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+        slice_range(rs, dg, s, m, lo, hi);
+        cols = a.Lci;
+        vals = (const T *)a.Lv;
+        out = MODE == M_TRSV ? (T *)a.y : (T *)a.xs;
+        vec = out;
+        first = (const T *)a.b;
+        if (owner) d = load_diag<T>(a, vals, dg, row, gl);
+    } else if constexpr (MODE == M_SPMV_TRSV) {
+        const int ra = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1);
+        out = (T *)a.y;
+        vec = out;
+        vec2 = (const T *)a.xin;
+        first = (const T *)a.b;
+        if (a.Lv == nullptr) {
+            dp = __ldg(a.a_diag + row);
+            slice_range(ra, re, s, m, lo, hi);
+            cols = a.Mci;
+            vals = (const T *)a.Mv;
+            if (owner) d = load_diag<T>(a, vals, dp, row, gl);
+        } else {
+            const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+            slice_range(rs, dg, s, m, lo, hi);
+            slice_range(ra, re, s, m, lo2, hi2);
+            cols = a.Lci;
+            vals = (const T *)a.Lv;
+            cols2 = a.Mci;
+            vals2 = (const T *)a.Mv;
+            if (owner) d = load_diag<T>(a, vals, dg, row, gl);
+        }
+    } else if constexpr (MODE == M_ADJ_SPMV_TRSV || MODE == M_ADJ_TRSV_SPMV) {
+        const int ls0 = __ldg(a.LTrp + row), le = __ldg(a.LTrp + row + 1);   // L^T row: L_jj first
+        slice_range(ls0 + 1, le, s, m, lo, hi);
+        cols = a.LTci;
+        vals = (const T *)a.LTv;
+        out = (T *)a.gb;
+        vec = out;
+        if (owner) d = load_diag<T>(a, vals, ls0, row, gl);
+        if constexpr (MODE == M_ADJ_SPMV_TRSV) {
+            first = (const T *)a.gy;
+        } else {
+            const int ms = __ldg(a.MTrp + row), me = __ldg(a.MTrp + row + 1);
+            slice_range(ms, me, s, m, lo2, hi2);
+            cols2 = a.MTci;
+            vals2 = (const T *)a.MTv;
+            vec2 = (const T *)a.gy;
+            sign2 = T(-1);   // lam_j = (u_j - sum L^T lam) / L_jj with u = M^T gy: p = sum L^T lam - u
+        }
+    }
+    (void)tag;
+    for (int c0 = 0; c0 < k; c0 += kt) {
+        const int c = c0 + cl;
+        const bool act = c < k;
+        // this slice's share p of the row's total, which the owner subtracts from `first`:
+        // p = (waited-for part) + sign2 * (part that waits for nothing)
+        T p;
+        if (dp >= 0) {
+            T ax, az;
+            gs_row_dot<T, VU>(cols, vals, lo + ls, dp, hi, S, vec2, out, k, c, act, a.st, a.timeout_ns, row, ok, ax,
+                              az);
+            p = slice_sum<LPR>(ax, kt, gmask) + slice_sum<LPR>(az, kt, gmask);
+        } else {
+            // the part that waits for nothing first, so that only the waited-for part follows
+            // the last input
+            T pf = T(0);
+            if (cols2) {
+                T af = row_dot<T, D_NONE, false>(cols2, nullptr, vals2, lo2 + ls, hi2, S, vec2, k, c, act, nullptr, 0u,
+                                                 a.st, a.timeout_ns, row, ok);
+                pf = sign2 * slice_sum<LPR>(af, kt, gmask);
+            }
+            T aw = row_dot<T, D_VALUE, false, VU>(cols, nullptr, vals, lo + ls, hi, S, vec, k, c, act, nullptr, 0u, a.st,
+                                                   a.timeout_ns, row, ok);
+            p = slice_sum<LPR>(aw, kt, gmask) + pf;
+        }
+        if (!owner) {
+            if (ls == 0 && act) put_value(parts + (size_t)(slot + s) * k + c, p);
+            continue;
+        }
+        if (ls == 0 && act) {
+            T tot = T(0);
+            for (int h = 0; h < m - 1 && ok; ++h)
+                tot += poll_value(parts + (size_t)(slot + h) * k + c, a.st, a.timeout_ns, row, ok);
+            tot += p;
+            const T f = first ? __ldg(first + (size_t)row * k + c) : T(0);
+            put_value(out + (size_t)row * k + c, finish_row<T>(a, f - tot, d));
+        }
+    }
+    return group_ok<LPR>(ok, gmask);
+}
+
 // Modes with value-flag launches (k = 1; IC0 modes for any k when the pair lists exist).
 constexpr bool mode_has_vf(int m) {
     return m == M_TRSV_SPMV || m == M_TRSV || m == M_SPMV_TRSV || m == M_ADJ_TRSV_SPMV || m == M_ADJ_SPMV_TRSV ||
@@ -1093,9 +1216,9 @@ constexpr int kMinBlocksIc0 = 4;
 
 // Next ticket of a team (its first lane draws it; the caller broadcasts it when needed, so
 // the atomic's latency overlaps the current partition's work).
-__device__ __forceinline__ int draw_ticket(const ExecArgs &a, int tl) {
+__device__ __forceinline__ int draw_ticket(const ExecArgs &a, int tl, int nunits) {
     if (tl != 0) return 0;
-    return ld_relaxed_u32(&a.st->abort) ? a.n_parts : (int)atomicAdd(&a.st->ticket, 1u);
+    return ld_relaxed_u32(&a.st->abort) ? nunits : (int)atomicAdd(&a.st->ticket, 1u);
 }
 
 // A warp is split into 32/TEAM teams of TEAM lanes; a team runs one partition at a time
@@ -1121,7 +1244,10 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
     // With two classes (separated schedules) teams [0, teams0) run the class-0 list and the
     // others the class-1 list, each round robin in increasing order; second-kernel rows then
     // never hold up a team that the dependence chain is waiting for.
-    int idx = team, stride = nteams, base = 0, end = a.n_parts;
+    // With split long rows the units are the entries of a.xlist (partition, slice, slices,
+    // partial slot), in queue order; otherwise the partitions themselves.
+    const int nunits = a.xlist ? a.nx : a.n_parts;
+    int idx = team, stride = nteams, base = 0, end = nunits;
     if (!a.dynamic && a.plist) {
         if (team < a.teams0) {
             stride = a.teams0;
@@ -1133,27 +1259,52 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
             end = a.n_parts - a.n_parts0;
         }
     }
-    auto part_at = [&](int i) { return i < end ? (a.plist ? __ldg(a.plist + base + i) : base + i) : a.n_parts; };
-    int p = a.dynamic ? __shfl_sync(tmask, draw_ticket(a, tl), tbase) : part_at(idx);
-    while (p < a.n_parts) {
-        const int pn_first = a.dynamic ? draw_ticket(a, tl) : 0;
+    auto unit_at = [&](int i) { return i < end ? (a.plist ? __ldg(a.plist + base + i) : base + i) : nunits; };
+    int u = a.dynamic ? __shfl_sync(tmask, draw_ticket(a, tl, nunits), tbase) : unit_at(idx);
+    while (u < nunits) {
+        const int un_first = a.dynamic ? draw_ticket(a, tl, nunits) : 0;
+        int p = u;
+        int4 sl = make_int4(u, 0, 1, 0);
+        if (a.xlist) {
+            sl = __ldg(a.xlist + u);
+            p = sl.x;
+        }
         const int q0 = __ldg(a.part_ptr + p), q1 = __ldg(a.part_ptr + p + 1);
+        if constexpr (VF && (MODE == M_TRSV || MODE == M_TRSV_SPMV || MODE == M_SPMV_TRSV || MODE == M_ADJ_SPMV_TRSV ||
+                             MODE == M_ADJ_TRSV_SPMV)) {
+            if (sl.z > 1) {
+                // one slice of a long row split over several teams
+                const unsigned o = (unsigned)__ldg(a.order + q0);
+                if (ok)
+                    ok = run_slice<MODE, T, TEAM, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), sl.y,
+                                                                     sl.z, sl.w, tl, tmask);
+                if (!__all_sync(tmask, ok)) break;
+                if (a.dynamic) u = __shfl_sync(tmask, un_first, tbase);
+                else {
+                    idx += stride;
+                    u = ld_relaxed_u32(&a.st->abort) ? nunits : unit_at(idx);
+                }
+                continue;
+            }
+        }
         if (LPR < TEAM && a.part_wide[p]) {
             // a long row: the whole team runs it (the cut gives it a partition of its own)
             const unsigned o = (unsigned)__ldg(a.order + q0);
-            if (ok) ok = run_item<MODE, T, TEAM, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl, tbase,
-                                                     tmask);
+            if (ok)
+                ok = run_item<MODE, T, TEAM, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl,
+                                                                    tbase, tmask);
         } else {
             for (int q = q0 + grp; q < q1 && ok; q += G) {
                 const unsigned o = (unsigned)__ldg(a.order + q);
-                ok = run_item<MODE, T, LPR, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl, gbase, gmask);
+                ok = run_item<MODE, T, LPR, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl,
+                                                                   gbase, gmask);
             }
         }
         if (!__all_sync(tmask, ok)) break;
-        if (a.dynamic) p = __shfl_sync(tmask, pn_first, tbase);
+        if (a.dynamic) u = __shfl_sync(tmask, un_first, tbase);
         else {
             idx += stride;
-            p = ld_relaxed_u32(&a.st->abort) ? a.n_parts : part_at(idx);
+            u = ld_relaxed_u32(&a.st->abort) ? nunits : unit_at(idx);
         }
     }
     __syncwarp();

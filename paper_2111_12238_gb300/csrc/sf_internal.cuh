@@ -92,6 +92,11 @@ struct ExecArgs {
     // position of the diagonal in every row of M (= A): ILU0 rows, and SpMV -> SpTRSV rows that
     // read L = tril(A) from A's storage (shared storage, Lv == NULL); else NULL
     const int *a_diag;
+    // long rows split at execution time: queue units (partition, slice, slices, first partial
+    // slot) and the helpers' partial sums (slots x k values, value flags); xlist NULL: none
+    const int4 *xlist;
+    int nx;
+    void *parts;
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)

@@ -61,7 +61,11 @@ class SfInfo(C.Structure):
                 ("split_pct", C.c_int32), ("adj_split_pct", C.c_int32),
                 ("g2_placement", C.c_int32), ("adj_g2_placement", C.c_int32),
                 ("min_blocks", C.c_int32), ("adj_min_blocks", C.c_int32),
-                ("ic0_pairs", C.c_int64), ("ic0_use_pairs", C.c_int32), ("reserved3", C.c_int32)]
+                ("ic0_pairs", C.c_int64), ("ic0_use_pairs", C.c_int32), ("reserved3", C.c_int32),
+                ("slice_cost", C.c_int64), ("adj_slice_cost", C.c_int64),
+                ("slice_units", C.c_int32), ("adj_slice_units", C.c_int32),
+                ("max_slices", C.c_int32), ("adj_max_slices", C.c_int32),
+                ("fwd_rhs_tile", C.c_int32), ("adj_rhs_tile", C.c_int32)]
 
 
 class SparseFusionError(RuntimeError):
@@ -93,6 +97,8 @@ _SIGS = {
     "sf_schedule_reblock": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P]),
     "sf_schedule_export_blocks": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "sf_schedule_set_split": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_set_slices": (C.c_int, [_P, C.c_int32, C.c_int64, _P]),
+    "sf_schedule_set_rhs_tile": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_replace": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "sf_schedule_set_occupancy": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_set_ic0_pairs": (C.c_int, [_P, C.c_int32]),
@@ -342,6 +348,15 @@ class Schedule:
         teams (separated schedules; 0 = one class)."""
         _check(load_library().sf_schedule_set_split(self.handle, int(which), int(class0_pct)),
                "sf_schedule_set_split")
+
+    def set_slices(self, which=-1, cost_per_slice=0, stream=None):
+        """Split rows costlier than cost_per_slice over several teams (0: off)."""
+        _check(load_library().sf_schedule_set_slices(self.handle, which, int(cost_per_slice), _stream(stream)),
+               "sf_schedule_set_slices")
+
+    def set_rhs_tile(self, which=-1, rhs_tile=0):
+        """Right-hand-side columns a row's lanes handle side by side (0: automatic)."""
+        _check(load_library().sf_schedule_set_rhs_tile(self.handle, which, int(rhs_tile)), "sf_schedule_set_rhs_tile")
 
     def set_timeout(self, ns: int):
         _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")

@@ -179,7 +179,7 @@ sf_status sf_execute(const sf_schedule *sch, sf_dtype dt, int32_t k, const void 
  *    -sum_c lam_ic z_jc, gM_vals (pattern of A) with gA_ij = -sum_c lam_ic x_in_jc.
  * Launches: the values of L^T and M^T (A^T) are first gathered into transposed order in
  * library-owned buffers, then the fused pass runs on the transposed schedule, then the value
- * gradients are written by a streaming pass over the rows of L and M (A).
+ * gradients are written by a streaming pass over the entries of L and M (A).
  * Other pairs return SF_ERR_UNSUPPORTED. Same stream and ownership rules as sf_execute. */
 sf_status sf_adjoint(const sf_schedule *sch, sf_dtype dt, int32_t k, const void *L_vals,
                      const void *M_vals, const void *x_in, const void *saved, const void *gy,
@@ -399,6 +399,19 @@ void sf_schedule_destroy(sf_schedule *sch);
 #define SF_NOALLOC_SCRATCH_BYTES (256 + 8 * SF_NOALLOC_MAX_ROWS)
 sf_status sf_trsv_spmv_noalloc(sf_dtype dt, const sf_csr *L, const sf_csr *M, const void *L_vals,
                                const void *M_vals, const void *b, void *y, void *stream);
+
+/* Measurement helpers for the roofline of the executor (the paper has no counterpart; they
+ * compute nothing of the method). Both are asynchronous on `stream`; the caller times them with
+ * CUDA events.
+ *  sf_bench_fma: the FMA rate of the GPU in the given element type: blocks x 256 threads, each
+ *    running 8 independent chains of `iters` fused multiply-adds, i.e. blocks * 256 * 16 * iters
+ *    flops. sink: device buffer of >= 256 elements (not written).
+ *  sf_bench_hop: the latency of handing one value between two SMs through L2 (one relaxed
+ *    store, one polling relaxed load), `hops` (even, >= 2) times in alternation by two resident
+ *    blocks. word: one zeroed device uint32; out: two zeroed device uint64, out[0] receives the
+ *    elapsed ns, out[1] = 1 when a poll gave up after 1 s (never a hang). */
+sf_status sf_bench_fma(sf_dtype dt, int32_t blocks, int32_t iters, void *sink, void *stream);
+sf_status sf_bench_hop(int32_t hops, void *word, void *out, void *stream);
 
 const char *sf_status_string(sf_status s);
 

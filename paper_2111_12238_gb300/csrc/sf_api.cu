@@ -156,6 +156,8 @@ struct sf_schedule {
     // and whether L's pattern is tril(A)'s (then SpMV -> SpTRSV may read L from A's storage)
     int *a_diag = nullptr;
     bool tril_ok = false;
+    // adjoint schedules: the row of every entry of L and of M (value-gradient passes)
+    int *L_row = nullptr, *M_row = nullptr;
     std::mutex mu;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -502,7 +504,11 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
         if (st != SF_OK) return st;
         S->LTv = S->keep.alloc(8 * (size_t)std::max<long long>(S->L.nnz, 1));
         S->MTv = S->keep.alloc(8 * (size_t)std::max<long long>(S->M.nnz, 1));
-        if (!S->LTv || !S->MTv) return fail(SF_ERR_OOM, "inspector: out of device memory");
+        S->L_row = (int *)S->keep.alloc(sizeof(int) * (size_t)std::max<long long>(S->L.nnz, 1));
+        S->M_row = (int *)S->keep.alloc(sizeof(int) * (size_t)std::max<long long>(S->M.nnz, 1));
+        if (!S->LTv || !S->MTv || !S->L_row || !S->M_row) return fail(SF_ERR_OOM, "inspector: out of device memory");
+        SF_CK(row_of_entries(S->L, S->L_row, s), "inspector: rows of entries");
+        SF_CK(row_of_entries(S->M, S->M_row, s), "inspector: rows of entries");
     }
     S->reuse = reuse_ratio(S->pair, S->n, S->L.nnz, S->hasM ? S->M.nnz : 0);
     SF_CK(cudaStreamSynchronize(s), "inspector");
@@ -993,17 +999,17 @@ SF_API sf_status sf_adjoint(const sf_schedule *S, sf_dtype dt, int32_t k, const 
     // 3. value gradients restricted to the patterns, streamed row by row
     if (S->pair == SF_TRSV_SPMV) {
         if (gL_vals)   // gL_ij = -sum_c lam_ic x_jc
-            SF_CK(launch_grad_rows(dtype, S->n, S->L.nnz, k, S->L.rowptr, S->L.colidx, gb, saved, -1.0, gL_vals, s),
+            SF_CK(launch_grad_entries(dtype, S->L.nnz, k, S->L_row, S->L.colidx, gb, saved, -1.0, gL_vals, s),
                   "adjoint gradients");
         if (gM_vals)   // gM_ij = sum_c gy_ic x_jc
-            SF_CK(launch_grad_rows(dtype, S->n, S->M.nnz, k, S->M.rowptr, S->M.colidx, gy, saved, 1.0, gM_vals, s),
+            SF_CK(launch_grad_entries(dtype, S->M.nnz, k, S->M_row, S->M.colidx, gy, saved, 1.0, gM_vals, s),
                   "adjoint gradients");
     } else {
         if (gL_vals)   // gL_ij = -sum_c lam_ic z_jc
-            SF_CK(launch_grad_rows(dtype, S->n, S->L.nnz, k, S->L.rowptr, S->L.colidx, gb, saved, -1.0, gL_vals, s),
+            SF_CK(launch_grad_entries(dtype, S->L.nnz, k, S->L_row, S->L.colidx, gb, saved, -1.0, gL_vals, s),
                   "adjoint gradients");
         if (gM_vals)   // gA_ij = -sum_c lam_ic x_in_jc
-            SF_CK(launch_grad_rows(dtype, S->n, S->M.nnz, k, S->M.rowptr, S->M.colidx, gb, x_in, -1.0, gM_vals, s),
+            SF_CK(launch_grad_entries(dtype, S->M.nnz, k, S->M_row, S->M.colidx, gb, x_in, -1.0, gM_vals, s),
                   "adjoint gradients");
     }
     return SF_OK;

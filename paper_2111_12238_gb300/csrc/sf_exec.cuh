@@ -536,24 +536,6 @@ __device__ __forceinline__ void gs_row_dot(const int *__restrict__ cols, const T
     if (np > 0 && ok) az += drain_values<T, kVPend>(z, pj, pv, (1u << np) - 1u, st, tmo, row, ok);
 }
 
-// out[e] = sign * sum_c coef(c) * vec[cols[e] * k + c] for e in [e0, e1): the pattern-
-// restricted outer product of the adjoint gradients. Slice s = gl / kt takes every S-th
-// entry, its kt lanes split the right-hand-side columns.
-template <typename T, int LPR, typename Coef>
-__device__ __forceinline__ void grad_row(const int *__restrict__ cols, int e0, int e1, Coef coef,
-                                         const T *__restrict__ vec, int k, int kt, int gl, int gbase,
-                                         T sign, T *out) {
-    const int S = LPR / kt, s = gl / kt, cl = gl % kt;
-    const unsigned smask = (kt == 32) ? 0xffffffffu : (((1u << kt) - 1u) << (gbase + s * kt));
-    for (int e = e0 + s; e < e1; e += S) {
-        const int j = __ldg(cols + e);
-        T part = T(0);
-        for (int c = cl; c < k; c += kt) part += coef(c) * __ldg(vec + (size_t)j * k + c);
-        part = col_sum(part, kt, smask);
-        if (cl == 0) out[e] = sign * part;
-    }
-}
-
 template <int LPR>
 __device__ __forceinline__ bool group_ok(bool ok, unsigned gmask) {
     return !__any_sync(gmask, !ok);

@@ -1,6 +1,9 @@
 // Executor instantiations: the adjoint pass of SpTRSV -> SpMV (that of SpMV -> SpTRSV is in
 // sf_exec_adj2.cu), plus the adjoint's two streaming helpers (values in transposed order,
-// and the pattern-restricted value gradients).
+// and the pattern-restricted value gradients, one thread per entry).
+#include <algorithm>
+#include <cstdint>
+
 #include "sf_exec.cuh"
 
 namespace sf {
@@ -33,53 +36,75 @@ cudaError_t launch_gather_vals(int dtype, long long nnz, const int *perm, const 
     return cudaGetLastError();
 }
 
-// out[e] = sign * sum_c coef[i*k+c] * vec[ci[e]*k+c] for every entry e of row i; one group of
-// LPR lanes per row, rows in order (coalesced over the pattern).
-template <typename T, int LPR>
-__global__ void __launch_bounds__(256) k_grad_rows(int n, int k, int kt, const int *__restrict__ rp,
-                                                   const int *__restrict__ ci, const T *__restrict__ coef,
-                                                   const T *__restrict__ vec, T sign, T *__restrict__ out) {
-    constexpr int G = 32 / LPR;
-    const int lane = threadIdx.x & 31, grp = lane / LPR, gl = lane % LPR, gbase = grp * LPR;
-    const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long r0 = warp * G; r0 < n; r0 += nwarps * G) {
-        const long long i = r0 + grp;
-        if (i >= n) continue;
-        const T *cr = coef + (size_t)i * k;
-        grad_row<T, LPR>(ci, __ldg(rp + i), __ldg(rp + i + 1), [&](int c) { return __ldg(cr + c); }, vec, k, kt, gl,
-                         gbase, sign, out);
+// out[e] = sign * sum_c coef[i*k+c] * vec[ci[e]*k+c] for every entry e (row i = row_of[e]):
+// the pattern-restricted outer products of the adjoint's value gradients. One thread per entry,
+// consecutive threads on consecutive entries (coalesced pattern reads and stores; the coef row
+// is shared by a row's entries and stays in L1), the k products of an entry summed in column
+// order from V-wide vector loads (V = 2 doubles or 4 floats when k allows the alignment), so a
+// thread has k / V independent loads in flight and no lane waits on another.
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float4; };
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(256) k_grad_entries(long long nnz, int k, const int *__restrict__ row_of,
+                                                      const int *__restrict__ ci, const T *__restrict__ coef,
+                                                      const T *__restrict__ vec, T sign, T *__restrict__ out) {
+    using VT = typename Vec2<T>::type;
+    constexpr int V = sizeof(VT) / sizeof(T);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (long long)gridDim.x * blockDim.x) {
+        const T *a = coef + (size_t)__ldg(row_of + e) * k;
+        const T *b = vec + (size_t)__ldg(ci + e) * k;
+        T sum = T(0);
+        if constexpr (VEC) {
+#pragma unroll 4
+            for (int c = 0; c < k; c += V) {
+                const VT va = __ldg((const VT *)(a + c)), vb = __ldg((const VT *)(b + c));
+                if constexpr (V == 2) {
+                    sum += va.x * vb.x;
+                    sum += va.y * vb.y;
+                } else {
+                    sum += va.x * vb.x;
+                    sum += va.y * vb.y;
+                    sum += va.z * vb.z;
+                    sum += va.w * vb.w;
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int c = 0; c < k; ++c) sum += __ldg(a + c) * __ldg(b + c);
+        }
+        out[e] = sign * sum;
     }
 }
 
-cudaError_t launch_grad_rows(int dtype, int n, long long nnz, int k, const int *rp, const int *ci, const void *coef,
-                             const void *vec, double sign, void *out, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+cudaError_t launch_grad_entries(int dtype, long long nnz, int k, const int *row_of, const int *ci, const void *coef,
+                                const void *vec, double sign, void *out, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int kt = 1;
-    while (kt < k && kt < 32) kt <<= 1;
-    const long long mean = (nnz + n - 1) / n;
-    int lpr = kt;
-    while (lpr < 32 && lpr * 4 < mean * kt) lpr <<= 1;    // about four entries per slice
-    const long long groups_per_block = 8LL * (32 / lpr);
-    long long blocks = (n + groups_per_block - 1) / groups_per_block;
-    if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
-#define SF_G(T, L) k_grad_rows<T, L><<<(unsigned)blocks, 256, 0, s>>>(n, k, kt, rp, ci, (const T *)coef, (const T *)vec, (T)sign, (T *)out); return cudaGetLastError()
+    const long long blocks = std::max<long long>(1, std::min<long long>((nnz + 255) / 256, (long long)sms * 32));
+    // vector loads need every row of coef and vec to start on a 16-byte boundary
+    const int V = dtype == 0 ? 2 : 4;
+    const bool vec_ok = k % V == 0 && ((uintptr_t)coef % 16) == 0 && ((uintptr_t)vec % 16) == 0;
     if (dtype == 0) {
-        switch (lpr) {
-            case 1: SF_G(double, 1); case 2: SF_G(double, 2); case 4: SF_G(double, 4);
-            case 8: SF_G(double, 8); case 16: SF_G(double, 16); case 32: SF_G(double, 32);
-        }
+        if (vec_ok)
+            k_grad_entries<double, true><<<(unsigned)blocks, 256, 0, s>>>(nnz, k, row_of, ci, (const double *)coef,
+                                                                         (const double *)vec, sign, (double *)out);
+        else
+            k_grad_entries<double, false><<<(unsigned)blocks, 256, 0, s>>>(nnz, k, row_of, ci, (const double *)coef,
+                                                                          (const double *)vec, sign, (double *)out);
     } else {
-        switch (lpr) {
-            case 1: SF_G(float, 1); case 2: SF_G(float, 2); case 4: SF_G(float, 4);
-            case 8: SF_G(float, 8); case 16: SF_G(float, 16); case 32: SF_G(float, 32);
-        }
+        if (vec_ok)
+            k_grad_entries<float, true><<<(unsigned)blocks, 256, 0, s>>>(nnz, k, row_of, ci, (const float *)coef,
+                                                                        (const float *)vec, (float)sign, (float *)out);
+        else
+            k_grad_entries<float, false><<<(unsigned)blocks, 256, 0, s>>>(nnz, k, row_of, ci, (const float *)coef,
+                                                                         (const float *)vec, (float)sign, (float *)out);
     }
-#undef SF_G
-    return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace sf

@@ -900,6 +900,11 @@ cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci
     return cudaStreamSynchronize(s);   // `last` and `h` live on this stack frame
 }
 
+cudaError_t row_of_entries(const DevCsr &m, int *row_of, cudaStream_t s) {
+    if (m.n_rows > 0 && m.nnz > 0) k_row_of<<<grid_for(m.n_rows, 256), 256, 0, s>>>(m.n_rows, m.rowptr, row_of);
+    return cudaGetLastError();
+}
+
 // Diagonal positions of A's rows and a comparison of L with tril(A): a_diag[i] = position of
 // A_ii (or -1); bit 0 of *bad: a row of A misses its diagonal; bit 1: L's row differs from
 // the lower part of A's row (diagonal included).

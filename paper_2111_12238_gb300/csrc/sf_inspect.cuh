@@ -66,6 +66,8 @@ cudaError_t check_pattern(const DevCsr &m, int lower, unsigned long long *status
 // a_diag[i] = position of A_ii in row i of A (-1: missing); *bad_host bit 0: a diagonal is
 // missing, bit 1: L's pattern is not tril(A)'s. Synchronises s.
 cudaError_t tril_map(const DevCsr &A, const DevCsr &L, int *a_diag, unsigned *bad_host, cudaStream_t s, Arena &ar);
+// row_of[e] = the row of entry e of m.
+cudaError_t row_of_entries(const DevCsr &m, int *row_of, cudaStream_t s);
 cudaError_t transpose_csr(const DevCsr &src, DevCsrT &dst, cudaStream_t s, Arena &ar, Arena &keep);
 cudaError_t kahn_levels(long long nv, int n1, const int *s1rp, const int *s1ci, const int *s2rp, const int *s2ci,
                         int *level, int *depth_out, cudaStream_t s, Arena &ar, bool *timed_out);

@@ -155,10 +155,11 @@ cudaError_t launch_exec_ic0_alone(int dtype, int lpr, bool vf, int team, int min
 int occupancy_ic0_alone(int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_adj(int mode, int dtype, int lpr, bool vf, int team, int minb);
 // Adjoint helpers: dst[t] = src[perm[t]] (values in transposed order), and the value
-// gradients out[e] = sign * sum_c coef[i*k+c] * vec[col(e)*k+c] over the rows i of a pattern.
+// gradients out[e] = sign * sum_c coef[row_of[e]*k+c] * vec[ci[e]*k+c] over every entry of a
+// pattern (row_of: the row of each entry).
 cudaError_t launch_gather_vals(int dtype, long long nnz, const int *perm, const void *src, void *dst, cudaStream_t s);
-cudaError_t launch_grad_rows(int dtype, int n, long long nnz, int k, const int *rp, const int *ci, const void *coef,
-                             const void *vec, double sign, void *out, cudaStream_t s);
+cudaError_t launch_grad_entries(int dtype, long long nnz, int k, const int *row_of, const int *ci, const void *coef,
+                                const void *vec, double sign, void *out, cudaStream_t s);
 // Sets the thread-local text returned by sf_last_error_detail.
 void set_error_detail(const char *msg);
 cudaError_t launch_spmv(int dtype, int lpr, int kt, int nrows, int k, const int *rp, const int *ci,

@@ -106,6 +106,8 @@ _SIGS = {
     "sf_schedule_launches": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "sf_schedule_debug_swap": (C.c_int, [_P, C.c_int64, C.c_int64]),
     "sf_schedule_destroy": (None, [_P]),
+    "sf_bench_fma": (C.c_int, [C.c_int, C.c_int32, C.c_int32, _P, _P]),
+    "sf_bench_hop": (C.c_int, [C.c_int32, _P, _P, _P]),
     "sf_status_string": (C.c_char_p, [C.c_int]),
     "sf_last_error_detail": (C.c_int, [C.c_char_p, C.c_size_t]),
 }
@@ -436,6 +438,37 @@ def spmv(M: DeviceCsr, vals: torch.Tensor, x: torch.Tensor, b: Optional[torch.Te
     _check(lib.sf_spmv(_dtype_code(x.dtype), k, C.byref(Ms), _ptr(vals, "vals"), _ptr(x, "x"), _ptr(b, "b"),
                        _ptr(y, "y"), _stream(stream)), "sf_spmv")
     return y
+
+
+# ------------------------------------------------------------------------------ measurement
+def bench_fma_tflops(dtype=torch.float64, iters=4096, reps=5, stream=None) -> float:
+    """Measured fused multiply-add rate of the current GPU (TFLOP/s, best of `reps`)."""
+    lib = load_library()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    blocks = props.multi_processor_count * 8
+    sink = torch.empty(256, dtype=dtype, device="cuda")
+    best = 0.0
+    for _ in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _check(lib.sf_bench_fma(_dtype_code(dtype), blocks, iters, _ptr(sink), _stream(stream)), "sf_bench_fma")
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = max(best, blocks * 256 * 16 * iters / (ms * 1e-3) / 1e12)
+    return best
+
+
+def bench_hop_ns(hops=20000, stream=None) -> float:
+    """Measured latency (ns) of one value handed between two SMs through L2."""
+    lib = load_library()
+    word = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _check(lib.sf_bench_hop(int(hops), _ptr(word), _ptr(out), _stream(stream)), "sf_bench_hop")
+    o = out.cpu().tolist()
+    if o[1]:
+        raise SparseFusionError(5, "sf_bench_hop", "a poll gave up")
+    return o[0] / hops
 
 
 # ------------------------------------------------------------------------------ autograd

@@ -309,8 +309,10 @@ sf_status sf_schedule_set_exec_events(sf_schedule *sch, int32_t which, void *ev_
  * variants compiled for three (four for IC0) resident 256-thread blocks per SM, which suits
  * schedules bound by the number of rows in flight (many independent instances, wide
  * wavefronts). The variants exist for value-flag launches (k = 1) with 1, 2 or 4 lanes per
- * row and 32-lane teams, and for IC0 launches with 32 lanes per row; other launches use the
- * default kernels. No GPU work. */
+ * row and 32-lane teams, and for IC0 launches with 32 lanes per row. 2 selects variants for
+ * two resident blocks (128 registers) of value-flag launches with 16 or 32 lanes per row (many
+ * right-hand sides): twice the teams, each further ahead of the dependence chain. Other
+ * launches use the default kernels. No GPU work. */
 sf_status sf_schedule_set_occupancy(sf_schedule *sch, int32_t which, int32_t min_blocks);
 
 /* IC0 schedules (SF_IC0_TRSV, SF_IC0; §2.1 up-looking zero-fill factor): entry (i, j) of

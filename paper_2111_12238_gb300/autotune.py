@@ -201,6 +201,17 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
         trials.append(dict(c, ms=ms))
         if ms < best["ms"]:
             best = trials[-1]
+    # wide rows with value flags (16 or 32 lanes): the two-block variants, twice the teams
+    if best is not None and best["exec"] == "partitions" and occupancy and not ic0 and \
+            best.get("lanes", 0) >= 16:
+        c = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "rt")}
+        c["occ"] = 2
+        _apply(sched, which, c, mean)
+        ms = _time(run, reps)
+        sched.check()
+        trials.append(dict(c, ms=ms))
+        if ms < best["ms"]:
+            best = trials[-1]
     # several right-hand sides: the best partition shape with the other right-hand-side tiles
     # (lanes at least the tile; 16 or more lanes publish rows through their values)
     if best is not None and best["exec"] == "partitions" and k > 1 and rhs_tiles:
@@ -221,8 +232,11 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     # long rows split over several teams at several costs per slice
     if best is not None and best["exec"] == "partitions" and slices:
         base = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "occ", "rt")}
-        for sc in slices:
-            c = dict(base, slices=sc)
+        bases = [base]
+        if k > 1 and (base.get("lanes") != 32 or base.get("rt", kt) != kt):
+            bases.append(dict(base, lanes=32, team=32, items=1, rt=kt))   # one pass over the columns
+        for b_, sc in [(b_, sc) for b_ in bases for sc in slices]:
+            c = dict(b_, slices=sc)
             _apply(sched, which, c, mean)
             inf2 = sched.info()
             if (inf2["slice_units"] if which == 0 else inf2["adj_slice_units"]) == 0:

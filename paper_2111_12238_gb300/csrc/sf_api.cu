@@ -570,11 +570,11 @@ sf_status get_scratch(const sf_schedule *Sc, size_t bytes, cudaStream_t s, void 
 
 int occupancy(int mode, int dtype, int lpr, bool vf, int team, int minb) {
     static std::mutex mu;
-    static int cache[M_COUNT][2][6][2][2][2] = {};
+    static int cache[M_COUNT][2][6][2][2][4] = {};
     int li = 0;
     while ((1 << li) < lpr) ++li;
     std::lock_guard<std::mutex> lk(mu);
-    int &c = cache[mode][dtype][li][vf ? 1 : 0][team == 8 ? 0 : 1][minb > 1 ? 1 : 0];
+    int &c = cache[mode][dtype][li][vf ? 1 : 0][team == 8 ? 0 : 1][std::min(std::max(minb, 1), 3)];
     if (!c) {
         if (mode == M_TRSV_SPMV || mode == M_TRSV) c = occupancy_fwd(mode, dtype, lpr, vf, team, minb);
         else if (mode == M_TRSV_TRSV || mode == M_ILU0_TRSV) c = occupancy_next(mode, dtype, lpr, vf, team, minb);
@@ -756,7 +756,7 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     a.xlist = nullptr;
     a.nx = 0;
     a.parts = nullptr;
-    if (sliced && blocks * teams_per_block >= d.max_m) {
+    if (sliced && blocks * teams_per_block >= d.max_m && d.n_slots * (long long)k <= 0x7fffffffLL) {
         // the helpers' partial sums start as the all-ones pattern
         const size_t es = dt == SF_F64 ? 8 : 4;
         const size_t bytes = es * (size_t)d.n_slots * (size_t)k;
@@ -1335,7 +1335,7 @@ SF_API sf_status sf_schedule_set_exec_events(sf_schedule *S, int32_t which, void
 SF_API sf_status sf_schedule_set_occupancy(sf_schedule *S, int32_t which, int32_t min_blocks) {
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
-    if (min_blocks != 0 && min_blocks != 1 && min_blocks != 3) return fail(SF_ERR_INVALID_ARG, "min_blocks must be 0, 1 or 3");
+    if (min_blocks < 0 || min_blocks > 3) return fail(SF_ERR_INVALID_ARG, "min_blocks must be 0, 1, 2 or 3");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w)

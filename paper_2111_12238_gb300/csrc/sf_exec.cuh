@@ -1041,8 +1041,9 @@ __device__ __forceinline__ void slice_range(int e0, int e1, int s, int m, int &l
 // products are cut into m chunks of entries; slices 0 .. m-2 (the helpers, earlier in the
 // queue) each add up their chunk and store the partial sums (one per right-hand-side column)
 // to a.parts[(slot + s) * k + c], every value its own flag; slice m-1 (the owner, queued after
-// its helpers) adds up the last chunk, whose inputs arrive last, waits for the helpers'
-// partials, sums them in slice order and finishes the row exactly as the item does. Several
+// its helpers) adds up the last chunk, whose inputs arrive last, gathers the helpers' partials
+// (all lanes, several loads in flight) and finishes the row exactly as the item does (the
+// partials summed in a fixed order). Several
 // teams thus stream one long row as its inputs arrive. Kinds: SpTRSV rows (SpTRSV -> SpMV
 // tag 0, SpTRSV alone), SpMV -> SpTRSV rows (A and L parts, or A's row in shared storage) and
 // the transposed solve rows of the adjoints.
@@ -1116,6 +1117,8 @@ __device__ bool run_slice(const ExecArgs &a, int tag, int row, int s, int m, int
     for (int c0 = 0; c0 < k; c0 += kt) {
         const int c = c0 + cl;
         const bool act = c < k;
+        // the owner's right-hand side, loaded before any wait
+        const T f = (owner && ls == 0 && act && first) ? __ldg(first + (size_t)row * k + c) : T(0);
         // this slice's share p of the row's total, which the owner subtracts from `first`:
         // p = (waited-for part) + sign2 * (part that waits for nothing)
         T p;
@@ -1141,14 +1144,28 @@ __device__ bool run_slice(const ExecArgs &a, int tag, int row, int s, int m, int
             if (ls == 0 && act) put_value(parts + (size_t)(slot + s) * k + c, p);
             continue;
         }
-        if (ls == 0 && act) {
-            T tot = T(0);
-            for (int h = 0; h < m - 1 && ok; ++h)
-                tot += poll_value(parts + (size_t)(slot + h) * k + c, a.st, a.timeout_ns, row, ok);
-            tot += p;
-            const T f = first ? __ldg(first + (size_t)row * k + c) : T(0);
-            put_value(out + (size_t)row * k + c, finish_row<T>(a, f - tot, d));
+        // the owner adds up its helpers' partial sums: the lane slices take every S-th helper,
+        // four loads in flight, then one reduction over the slices (a fixed order)
+        T help = T(0);
+        if (m > 1) {
+            T hs = T(0);
+            if (act)
+                for (int h0 = ls; h0 < m - 1 && ok; h0 += 4 * S) {
+                    int j[4];
+                    T xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int h = h0 + u * S;
+                        j[u] = h < m - 1 ? (slot + h) * k + c : -1;
+                    }
+                    ok = wait_values<T, 4>(parts, j, xv, a.st, a.timeout_ns, row);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (j[u] >= 0) hs += xv[u];
+                }
+            help = slice_sum<LPR>(hs, kt, gmask);
         }
+        if (ls == 0 && act) put_value(out + (size_t)row * k + c, finish_row<T>(a, f - (help + p), d));
     }
     return group_ok<LPR>(ok, gmask);
 }
@@ -1193,6 +1210,7 @@ __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, un
 // to four lanes per row) or four (64 registers: IC0 kernels with whole-warp rows, which fit
 // there without spilling), for schedules bound by the number of rows in flight.
 constexpr int kMinBlocksDefault = 1;
+constexpr int kMinBlocksWide = 2;   // value-flag kernels with 16 or 32 lanes per row: 128 registers
 constexpr int kMinBlocksHigh = 3;
 constexpr int kMinBlocksIc0 = 4;
 
@@ -1312,6 +1330,12 @@ const void *kernel_for_team(int dtype, int lpr, int minb) {
         }
     }
     if constexpr (VF && TEAM == 32) {
+        if (minb == kMinBlocksWide && (lpr == 16 || lpr == 32)) {
+            constexpr int H = kMinBlocksWide;
+            if (dtype == 0) return lpr == 16 ? (const void *)k_exec<MODE, double, 16, VF, 32, H>
+                                             : (const void *)k_exec<MODE, double, 32, VF, 32, H>;
+            return lpr == 16 ? (const void *)k_exec<MODE, float, 16, VF, 32, H> : (const void *)k_exec<MODE, float, 32, VF, 32, H>;
+        }
         if (minb >= kMinBlocksHigh) {
             constexpr int H = kMinBlocksHigh;
             if (dtype == 0) {

@@ -122,7 +122,7 @@ def test_rhs_tile_phase_for_several_right_hand_sides(fake_timing):
     fake_timing["sched"] = s
     r = autotune.tune(s, lambda: None, k=16, budget_s=60, use_cache=False)
     tiles = {t.get("rt") for t in r["trials"] if "rt" in t}
-    assert tiles == {1, 2, 4, 8, 32}
+    assert {1, 2, 4, 8, 32} <= tiles
     assert all(t["lanes"] >= t["rt"] for t in r["trials"] if "rt" in t)
     assert (r["rt"], r["lanes"]) == (8, 32) and s.state["rt"] == 8 and s.state["lanes"] == 32
 

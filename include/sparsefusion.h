@@ -375,28 +375,28 @@ void sf_schedule_destroy(sf_schedule *sch);
 
 /* Allocation-free fused SpTRSV -> SpMV, y = M L^-1 b with one right-hand side (k = 1).
  *
- * The paper has no counterpart: this entry point exists for callers that must not allocate
- * device memory at the point of the call, for instance code that runs while a stream is
- * being captured into a CUDA graph (allocation is not allowed there), latency-critical
- * loops that cannot afford the device-wide synchronisation cudaMalloc implies, or
- * applications whose memory is entirely owned by their own pool allocator. It needs no
- * inspector schedule (and so allocates nothing): rows run in their natural order (all
- * SpTRSV rows, then all SpMV rows), which is a valid order of the joint DAG because L is
- * lower triangular, and the intermediate x plus the launch state live in a fixed device
- * array compiled into the library.
+ * The paper has no counterpart: this entry point serves callers that must not allocate device
+ * memory at the point of the call - code that runs inside a custom allocator's own callbacks,
+ * applications whose device memory is all handed out in advance by their own pool or budget,
+ * and latency-critical loops that cannot wait for the device-wide synchronisation an
+ * allocation can imply. It needs no inspector schedule (and so allocates nothing): rows run in
+ * their natural order (all SpTRSV rows, then all SpMV rows), which is a valid order of the
+ * joint DAG because L is lower triangular, and the intermediate x plus the launch state live
+ * in a fixed device array compiled into the library.
  *
  *  L, M:   patterns as for sf_inspect with SF_TRSV_SPMV (n x n, n = L.n_rows); device
  *          pointers, caller-owned. They are checked on the GPU at every call.
  *  L_vals, M_vals, b (n x 1) inputs and y (n x 1) output: device pointers, caller-owned.
  *  n must not exceed SF_NOALLOC_MAX_ROWS (larger sizes return SF_ERR_INVALID_ARG).
  * Scratch: one array of SF_NOALLOC_SCRATCH_BYTES bytes per device, held by every GPU that
- * loads the library until the process exits. The first call on a device looks up that
- * array's address (cudaGetSymbolAddress), so make the first call on each device before
- * any stream capture. Every call resets the part of the array it uses, but all calls
- * share the one array: calls whose executions overlap on the GPU (other streams, other
- * host threads) race and give wrong results; serialise them.
+ * loads the library until the process exits. The first call on a device (and the first after
+ * the device's context was reset) looks up that array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture. Every call clears the
+ * part of the array it uses, but all calls share the one array: calls whose executions overlap
+ * on the GPU (other streams, other host threads) race and give wrong results; serialise them.
  * The call is stream-ordered and then synchronises `stream` to report the outcome:
- * SF_ERR_BAD_PATTERN, SF_ERR_TIMEOUT or SF_ERR_NONFINITE as for the scheduled path. */
+ * SF_ERR_BAD_PATTERN, SF_ERR_TIMEOUT or SF_ERR_NONFINITE (a zero diagonal of L) as for the
+ * scheduled path. */
 #define SF_NOALLOC_MAX_ROWS 1048576
 #define SF_NOALLOC_SCRATCH_BYTES (256 + 8 * SF_NOALLOC_MAX_ROWS)
 sf_status sf_trsv_spmv_noalloc(sf_dtype dt, const sf_csr *L, const sf_csr *M, const void *L_vals,

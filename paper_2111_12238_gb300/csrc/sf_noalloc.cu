@@ -1,7 +1,9 @@
 // Allocation-free fused SpTRSV -> SpMV (k = 1) for callers that cannot allocate device
-// memory when they call: the scratch of the fused executor (the intermediate x, the launch
-// state and the pattern-check words) lives in one file-scope device array, and the rows
-// run in their natural order, so no inspector schedule is needed.
+// memory when they call (a custom allocator's own callbacks, code whose device memory is fixed
+// in advance by a pool or a budget, latency-critical loops that must not wait for the
+// device-wide synchronisation an allocation can cause): the scratch of the fused executor (the
+// intermediate x, the launch state and the pattern-check words) lives in one file-scope device
+// array, and the rows run in their natural order, so no inspector schedule is needed.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -30,19 +32,51 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SF_NOALLOC_SCRA
 constexpr int kMaxDevices = 256;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array for the current device (looked up once per device).
+// Identifier of the current CUDA context (0 when the driver cannot tell): a reset of the device
+// creates a new context, in which the array has a new address.
+unsigned long long current_context_id() {
+    using get_ctx_t = int (*)(void **);
+    using get_id_t = int (*)(void *, unsigned long long *);
+    static get_ctx_t get_ctx = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = (get_ctx_t)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_t)f;
+        cudaGetLastError();
+        looked = true;
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_ctx && get_id && get_ctx(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Device address of the scratch array for the current device: looked up (cudaGetSymbolAddress,
+// with that device current) at the first call on the device, and again when the device's
+// context has changed since (after a device reset).
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;

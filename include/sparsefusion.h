@@ -335,15 +335,16 @@ sf_status sf_schedule_set_split(sf_schedule *sch, int32_t which, int32_t class0_
 
 /* Execution-time split of long rows (§3.1 vertex cost c(v) used to balance the load of the
  * executor, not only of partitions): in the forward (which = 0), adjoint (1) or both (-1)
- * schedules, every partition holding a single SpTRSV row, SpMV -> SpTRSV row or transposed
- * solve row (adjoints) whose cost exceeds cost_per_slice is run as m = ceil(cost /
- * cost_per_slice) slices (at most 32) by m teams: each slice streams a contiguous chunk of the
- * row's entries as their inputs arrive, m - 1 helpers store partial sums (library scratch of
- * m - 1 values per right-hand side, published by value), the owner slice (queued after its
- * helpers) adds them in slice order and finishes the row. Levels, order and partitions are
- * unchanged. Applies to launches that publish through values (k = 1, or 16 or more lanes per
- * row) of the partition executor; other launches run rows whole. 0 turns it off (default).
- * Synchronises `stream`; no launch of this schedule may be pending on another stream. */
+ * schedules, every SpTRSV row, SpMV -> SpTRSV row or transposed solve row (adjoints) whose cost
+ * exceeds cost_per_slice gets a partition of its own (the partitions are re-cut with the same
+ * cost target; levels and order are unchanged) and runs as m = ceil(cost / cost_per_slice)
+ * slices (at most 32) on m teams: each slice streams a contiguous chunk of the row's entries
+ * as their inputs arrive, m - 1 helpers store partial sums (library scratch of m - 1 values per
+ * right-hand side, published by value), the owner slice (queued after its helpers; its chunk,
+ * the latest columns, is half as long) adds them in slice order and finishes the row. Applies
+ * to launches that publish through values (k = 1, or 16 or more lanes per row) of the
+ * partition executor; other launches run rows whole. 0 turns it off (default). Synchronises
+ * `stream`; no launch of this schedule may be pending on another stream. */
 sf_status sf_schedule_set_slices(sf_schedule *sch, int32_t which, int64_t cost_per_slice, void *stream);
 
 /* Right-hand-side tile of the forward (0), adjoint (1) or both (-1) schedules: the columns of

@@ -233,8 +233,11 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     if best is not None and best["exec"] == "partitions" and slices:
         base = {kk: v for kk, v in best.items() if kk in ("exec", "lanes", "items", "team", "g2", "occ", "rt")}
         bases = [base]
-        if k > 1 and (base.get("lanes") != 32 or base.get("rt", kt) != kt):
-            bases.append(dict(base, lanes=32, team=32, items=1, rt=kt))   # one pass over the columns
+        if k > 1 and base.get("rt", kt) != kt:
+            # one pass over the columns (the widest tile) at the same lanes
+            bases.append({kk: v for kk, v in base.items() if kk != "rt"})
+        if k > 1 and base.get("lanes") != 32:
+            bases.append(dict({kk: v for kk, v in base.items() if kk != "rt"}, lanes=32, team=32, items=1))
         for b_, sc in [(b_, sc) for b_ in bases for sc in slices]:
             c = dict(b_, slices=sc)
             _apply(sched, which, c, mean)

@@ -283,8 +283,10 @@ sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Aren
         C = (long long)std::max(1, std::min(d.team / d.lpr, 8)) * mean;
     }
     d.C = C;
-    // rows much longer than a group's lanes can cover quickly get the whole warp
+    // rows much longer than a group's lanes can cover quickly get the whole warp, and rows to be
+    // split over several teams (cost above the slice cost) a partition of their own
     d.W = d.lpr < 32 ? 16LL * d.lpr + 1 : 0;
+    if (d.slice_cost > 0) d.W = d.W ? std::min(d.W, d.slice_cost) : d.slice_cost;
     e = cut_partitions(nv, Sx, cs, C, d.W, d.part_ptr, d.part_wide, &d.n_parts, s, tmp);
     if (e != cudaSuccess) return from_cuda(e, "partition cut");
     if (d.kind == K_SEP || d.kind == K_SEP_T) {
@@ -1380,14 +1382,19 @@ SF_API sf_status sf_schedule_set_slices(sf_schedule *S, int32_t which, int64_t c
     if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
     if (cost_per_slice < 0) return fail(SF_ERR_INVALID_ARG, "cost_per_slice must be >= 0");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
-    SF_CK(cudaStreamSynchronize((cudaStream_t)stream), "slices");
+    cudaStream_t s = (cudaStream_t)stream;
+    SF_CK(cudaStreamSynchronize(s), "slices");
+    Arena tmp;
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;
+        if (dirs[w]->slice_cost == cost_per_slice) continue;
         dirs[w]->slice_cost = cost_per_slice;
-        sf_status st = slice_dir(S, *dirs[w]);
+        // re-cut (same cost target): rows above the slice cost get partitions of their own
+        sf_status st = cut_dir(S, *dirs[w], dirs[w]->C, s, tmp);
         if (st != SF_OK) return st;
     }
+    SF_CK(cudaStreamSynchronize(s), "slices");
     return SF_OK;
 }
 

@@ -1030,11 +1030,13 @@ __device__ bool item_ilu0(const ExecArgs &a, int row, int gl) {
     return !__any_sync(full, !ok);
 }
 
-// Chunk s of m equal chunks of the entry range [e0, e1).
+// Chunk s of m chunks of the entry range [e0, e1): the m - 1 helper chunks are equal and the
+// owner's last chunk (the latest columns, whose inputs arrive last) is half as long, so less of
+// the row is left to walk after its last input.
 __device__ __forceinline__ void slice_range(int e0, int e1, int s, int m, int &lo, int &hi) {
-    const int chunk = (e1 - e0 + m - 1) / m;
+    const int chunk = (2 * (e1 - e0) + 2 * m - 2) / (2 * m - 1);
     lo = min(e1, e0 + s * chunk);
-    hi = min(e1, lo + chunk);
+    hi = s == m - 1 ? e1 : min(e1, lo + chunk);
 }
 
 // One slice of a long row split at execution time (whole team, value flags). The row's dot

@@ -110,7 +110,10 @@ typedef struct {
     int32_t exec_mode;        /* 0 (automatic) and 1: partitions; 2: row blocks; 3: row blocks
                                  with warp-specialised loading (cp.async); 4: row blocks with
                                  packed records and bulk copies (2-4: k = 1 with value flags;
-                                 the call fails when a block does not fit in shared memory).
+                                 the call fails when a block does not fit in shared memory);
+                                 5: one CTA runs the whole system, level segment by level
+                                 segment between CTA barriers, x in shared memory (SF_TRSV_SPMV
+                                 forward and SF_TRSV, k = 1, small n; one block of rows).
                                  The autotuner chooses between them. */
 } sf_options;
 
@@ -285,7 +288,8 @@ sf_status sf_schedule_replace(sf_schedule *sch, int32_t which, int32_t g2_placem
  * order of the forward (0), adjoint (1) or both (-1) schedules for block_rows rows
  * (0 keeps the current size), sets exec_mode (-1 keeps; 0 automatic, 1 partitions,
  * 2 row blocks, 3 warp-specialised row blocks, 4 row blocks with packed records, built
- * here) and the row-block lanes per row (1, 2, 4 or 32; 0 keeps; exec_modes 3 and 4 run one
+ * here, 5 the single-CTA executor, which needs one block of every row: block_rows 0 then
+ * means n) and the row-block lanes per row (1, 2, 4 or 32; 0 keeps; exec_modes 3 and 4 run one
  * consumer thread per row). Synchronises
  * `stream` before and after. */
 sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,

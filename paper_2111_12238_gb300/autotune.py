@@ -94,7 +94,10 @@ def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     sched.set_occupancy(which, c.get("occ", 1))
     sched.set_rhs_tile(which, c.get("rt", 0))
     sched.set_slices(which, c.get("slices", 0) if c["exec"] == "partitions" else 0)
-    if c["exec"] == "blocks":
+    if c["exec"] == "cta":
+        sched.reblock(which, 0, 5, 0)
+        sched.set_split(which, 0)
+    elif c["exec"] == "blocks":
         sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
         sched.set_split(which, 0)
     elif c["exec"] in ("ws", "tma"):
@@ -138,6 +141,8 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     pc = [(L, p, T) for L in lanes if L >= kt for T in teams if T >= L for p in items if p <= max(1, T // L) * 4]
     pc.sort(key=lambda c: (abs(c[0] - max(1, kt)), c[2] != 32, abs(c[1] - 8)))
     cands = [{"exec": "partitions", "lanes": L, "items": p, "team": T} for L, p, T in pc]
+    if k == 1 and blocks and sched.pair in ("trsv_spmv", "trsv") and which == 0 and inf["n"] <= 32768:
+        cands.insert(1, {"exec": "cta"})   # small systems: one CTA, x in shared memory
     if k == 1 and blocks:
         n = inf["n"]
         sizes = [B for B in block_rows if B <= 2 * max(n, 1)]
@@ -155,7 +160,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
             ms = _time(run, reps)
         except sf.SparseFusionError:
             # a row-block size whose shared-memory footprint does not fit this direction
-            if c["exec"] not in ("blocks", "ws", "tma"):
+            if c["exec"] not in ("blocks", "ws", "tma", "cta"):
                 raise
             continue
         sched.check()
@@ -168,7 +173,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     # with the teams split between the two partition classes
     if best is not None and separated and placements:
         bases = [best]
-        rb = [t for t in trials if t["exec"] in ("ws", "tma", "blocks")]
+        rb = [t for t in trials if t["exec"] in ("ws", "tma", "blocks", "cta")]
         if rb:
             rb_best = min(rb, key=lambda t: t["ms"])
             if rb_best is not best:
@@ -181,7 +186,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
                 _apply(sched, which, c, mean)
                 ms = _time(run, reps)
             except sf.SparseFusionError:
-                if c["exec"] not in ("blocks", "ws", "tma"):
+                if c["exec"] not in ("blocks", "ws", "tma", "cta"):
                     raise
                 continue
             sched.check()

@@ -180,7 +180,7 @@ sf_status validate_options(const sf_options *o) {
         return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     if (o->block_rows < 0 || o->block_rows > (1 << 20))
         return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
-    if (o->exec_mode < 0 || o->exec_mode > 4) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0 .. 4");
+    if (o->exec_mode < 0 || o->exec_mode > 5) return fail(SF_ERR_INVALID_ARG, "exec_mode must be 0 .. 5");
     if (o->blocks_per_sm < 0) return fail(SF_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
     if (o->flags & ~(SF_WANT_ADJOINT | SF_EPOCH_FLAGS | SF_DYNAMIC_QUEUE))
         return fail(SF_ERR_INVALID_ARG, "unknown option flags 0x%x", o->flags);
@@ -647,6 +647,19 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         return fail(SF_ERR_UNSUPPORTED, "L read from A's rows needs value flags: k = 1, or at least 16 lanes per row");
     // the row-block executors serve one right-hand side
     const bool rows1 = vf && !ic0 && k == 1 && !shared;
+    // single-CTA executor: small systems whose whole row-block order is one block
+    if (d.exec_mode == 5) {
+        if ((mode != M_TRSV_SPMV && mode != M_TRSV) || k != 1 || a.Lv == nullptr)
+            return fail(SF_ERR_UNSUPPORTED, "the single-CTA executor runs SpTRSV -> SpMV and SpTRSV with k = 1");
+        if (d.nb != 1) return fail(SF_ERR_UNSUPPORTED, "the single-CTA executor needs one block holding every row");
+        a.order = d.border;
+        a.seg_ptr = d.seg_ptr;
+        a.block_seg = d.block_seg;
+        cudaError_t e = launch_cta_exec(mode, dtype, S->L.nnz, d.nv, d.n_segs, s, a, d.ev_start, d.ev_stop);
+        if (e == cudaErrorInvalidValue) return fail(SF_ERR_UNSUPPORTED, "x does not fit in one CTA's shared memory");
+        if (e != cudaSuccess) return from_cuda(e, "single-CTA executor launch");
+        return SF_OK;
+    }
     // row-block executor with packed records and bulk copies
     if (rows1 && d.exec_mode == 4 && d.nb > 0) {
         const int nc = std::min(256, std::max(32, pow2_ceil(std::max(d.max_seg, 1))));
@@ -992,7 +1005,8 @@ SF_API sf_status sf_adjoint(const sf_schedule *S, sf_dtype dt, int32_t k, const 
     // 1. values of L^T and M^T (A^T) in transposed order, one coalesced gather each; the
     //    row-block executors of the SpTRSV -> SpMV adjoint read M^T only in their pre-pass
     //    (u = M^T gy), which then reads M's values through the permutation instead
-    a.mt_direct = (mode == M_ADJ_TRSV_SPMV && k == 1 && !S->epoch_flags && S->adj.exec_mode >= 2) ? 1 : 0;
+    a.mt_direct = (mode == M_ADJ_TRSV_SPMV && k == 1 && !S->epoch_flags && S->adj.exec_mode >= 2 &&
+                   S->adj.exec_mode <= 4) ? 1 : 0;
     SF_CK(launch_gather_vals(dtype, S->L.nnz, S->LT.perm, L_vals, S->LTv, s), "adjoint gather");
     if (!a.mt_direct) SF_CK(launch_gather_vals(dtype, S->M.nnz, S->MT.perm, M_vals, S->MTv, s), "adjoint gather");
     // 2. the fused pass on the transposed schedule
@@ -1273,7 +1287,7 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
     if (which < -1 || which > 1) return fail(SF_ERR_INVALID_ARG, "which must be -1, 0 or 1");
     if (block_rows < 0 || block_rows > (1 << 20)) return fail(SF_ERR_INVALID_ARG, "block_rows must be in [0, 2^20]");
-    if (exec_mode < -1 || exec_mode > 4) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1 .. 4");
+    if (exec_mode < -1 || exec_mode > 5) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1 .. 5");
     if (lanes_per_row != 0 && lanes_per_row != 1 && lanes_per_row != 2 && lanes_per_row != 4 && lanes_per_row != 32)
         return fail(SF_ERR_INVALID_ARG, "row-block lanes per row must be 1, 2, 4 or 32");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
@@ -1283,6 +1297,7 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;
+        if (exec_mode == 5 && !block_rows) block_rows = (int)std::min<long long>(1 << 20, ((long long)S->n + 31) / 32 * 32);
         if (block_rows && block_rows != dirs[w]->B) {
             sf_status st = block_dir(S, *dirs[w], block_rows, s, tmp);
             if (st != SF_OK) return st;
@@ -1313,10 +1328,11 @@ SF_API sf_status sf_schedule_launches(const sf_schedule *S, int32_t which, int32
     const int lpr = std::max(d.lpr, kt);
     const bool vf = !S->epoch_flags && vf_pair && (long long)S->n * k <= 0x7fffffffLL && (k == 1 || lpr >= 16);
     int n = 0;
-    if (vf && k == 1 && d.exec_mode >= 2 && d.nb > 0) n = 2 + (d.exec_mode == 4 ? 1 : 0);   // pre-pass(es) + executor
+    if (k == 1 && d.exec_mode == 5) n = 1;                                          // single-CTA executor
+    else if (vf && k == 1 && d.exec_mode >= 2 && d.nb > 0) n = 2 + (d.exec_mode == 4 ? 1 : 0);   // pre-pass(es) + executor
     else n = (vf ? 1 : 0) + 1;                                                  // value-flag reset + executor
     if (which == 1) {
-        const bool mt_direct = S->pair == SF_TRSV_SPMV && vf && k == 1 && d.exec_mode >= 2;
+        const bool mt_direct = S->pair == SF_TRSV_SPMV && vf && k == 1 && d.exec_mode >= 2 && d.exec_mode <= 4;
         n += 1 + (mt_direct ? 0 : 1) + 2;   // value gathers and both gradient passes
     }
     *count = n;

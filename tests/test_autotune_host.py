@@ -32,8 +32,8 @@ class FakeSched:
     def reblock(self, which, B, mode, lanes):
         if mode == 4 and self.tma_fails:
             raise sf.SparseFusionError(8, "sf_schedule_reblock", "does not fit")
-        if mode in (2, 3, 4):
-            self.state.update(exec={2: "blocks", 3: "ws", 4: "tma"}[mode], B=B, blanes=lanes)
+        if mode in (2, 3, 4, 5):
+            self.state.update(exec={2: "blocks", 3: "ws", 4: "tma", 5: "cta"}[mode], B=B, blanes=lanes)
         else:
             self.state["exec"] = "partitions"
 
@@ -91,7 +91,7 @@ def test_tuner_finds_and_applies_the_best_shape(fake_timing):
     assert not any("rt" in t for t in best["trials"])
     # every row-block executor was tried, and placements were tried on the best row-block shape too
     kinds = {t["exec"] for t in best["trials"]}
-    assert kinds == {"partitions", "ws", "tma", "blocks"}
+    assert kinds == {"partitions", "ws", "tma", "blocks", "cta"}
     assert any(t["exec"] != "partitions" and t.get("g2") == -1 for t in best["trials"])
 
 

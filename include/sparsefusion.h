@@ -111,9 +111,11 @@ typedef struct {
                                  with warp-specialised loading (cp.async); 4: row blocks with
                                  packed records and bulk copies (2-4: k = 1 with value flags;
                                  the call fails when a block does not fit in shared memory);
-                                 5: one CTA runs the whole system, level segment by level
-                                 segment between CTA barriers, x in shared memory (SF_TRSV_SPMV
-                                 forward and SF_TRSV, k = 1, small n; one block of rows).
+                                 5: one CTA per instance (the whole system, or each instance
+                                 of a batch) runs its joint DAG level segment by level segment
+                                 between CTA barriers, with x (and the order and L when they
+                                 fit) in shared memory; no waits between CTAs (SF_TRSV_SPMV
+                                 forward and SF_TRSV, k = 1; block_rows is then ignored).
                                  The autotuner chooses between them. */
 } sf_options;
 
@@ -286,12 +288,16 @@ sf_status sf_schedule_replace(sf_schedule *sch, int32_t which, int32_t g2_placem
  * independent part and 1 / L_ii, so first-kernel rows finish as (c - sum) * (1 / L_ii)
  * (one rounding more than a division). Rebuilds the block
  * order of the forward (0), adjoint (1) or both (-1) schedules for block_rows rows
- * (0 keeps the current size), sets exec_mode (-1 keeps; 0 automatic, 1 partitions,
- * 2 row blocks, 3 warp-specialised row blocks, 4 row blocks with packed records, built
- * here, 5 the single-CTA executor, which needs one block of every row: block_rows 0 then
- * means n) and the row-block lanes per row (1, 2, 4 or 32; 0 keeps; exec_modes 3 and 4 run one
- * consumer thread per row). Synchronises
- * `stream` before and after. */
+ * (0 keeps the current size, or takes the automatic size when leaving exec_mode 5), sets
+ * exec_mode (-1 keeps; 0 automatic, 1 partitions, 2 row blocks, 3 warp-specialised row
+ * blocks, 4 row blocks with packed records, built here, 5 the single-CTA executor: one block
+ * per instance, which needs block_rows = 0) and the row-block lanes per row (1, 2, 4 or 32;
+ * 0 keeps; exec_modes 3 and 4 run one consumer thread per row). For exec_mode 5 the last
+ * argument is the number of CTAs sharing an SM instead (1, 2 or 4, of 1024, 512 or 256
+ * threads and an equal share of the SM's shared memory; 0 automatic: 1 when every instance
+ * has an SM of its own, else 2). The single-CTA executor scales the diagonal by its
+ * reciprocal when L is staged in shared memory (one rounding more than a division), and
+ * divides otherwise. Synchronises `stream` before and after. */
 sf_status sf_schedule_reblock(sf_schedule *sch, int32_t which, int32_t block_rows, int32_t exec_mode,
                               int32_t lanes_per_row, void *stream);
 

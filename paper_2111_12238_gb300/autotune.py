@@ -95,7 +95,7 @@ def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     sched.set_rhs_tile(which, c.get("rt", 0))
     sched.set_slices(which, c.get("slices", 0) if c["exec"] == "partitions" else 0)
     if c["exec"] == "cta":
-        sched.reblock(which, 0, 5, 0)
+        sched.reblock(which, 0, 5, c.get("cps", 0))
         sched.set_split(which, 0)
     elif c["exec"] == "blocks":
         sched.reblock(which, c["block_rows"], 2, c["block_lanes"])
@@ -141,8 +141,11 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
     pc = [(L, p, T) for L in lanes if L >= kt for T in teams if T >= L for p in items if p <= max(1, T // L) * 4]
     pc.sort(key=lambda c: (abs(c[0] - max(1, kt)), c[2] != 32, abs(c[1] - 8)))
     cands = [{"exec": "partitions", "lanes": L, "items": p, "team": T} for L, p, T in pc]
-    if k == 1 and blocks and sched.pair in ("trsv_spmv", "trsv") and which == 0 and inf["n"] <= 32768:
-        cands.insert(1, {"exec": "cta"})   # small systems: one CTA, x in shared memory
+    if k == 1 and blocks and sched.pair in ("trsv_spmv", "trsv") and which == 0 and \
+            (inf["instances"] > 1 or inf["n"] <= 65536):
+        # small systems, or batches of independent instances: one CTA per instance, x on chip
+        cps = (2, 1, 4) if inf["instances"] > 1 else (1,)
+        cands[1:1] = [{"exec": "cta", "cps": c} for c in cps]
     if k == 1 and blocks:
         n = inf["n"]
         sizes = [B for B in block_rows if B <= 2 * max(n, 1)]

@@ -77,13 +77,16 @@ struct Dir {
     // row-block schedule (k = 1 executor with shared-memory dependences)
     int B = 0, nb = 0;
     int blpr = 1;               // lanes per row of the row-block executor (1, 4 or 32)
-    int exec_mode = 0;          // 0 automatic (partitions), 1 partitions, 2 row blocks
+    int exec_mode = 0;          // 0 automatic (partitions), 1 partitions, 2-4 row blocks, 5 one CTA per instance
     int *border = nullptr;      // order by (block, level, kernel, row)
     int2 *bdesc = nullptr;      // per position: entry range of the row waited on
     int *block_ptr = nullptr;
     int *seg_ptr = nullptr;     // level segments of the row-block order (n_segs + 1)
     int *block_seg = nullptr;   // first segment of every block (nb + 1)
     int n_segs = 0, max_seg = 0;
+    bool per_inst = false;      // blocks are the instances (single-CTA executor), not B rows
+    int *bperm = nullptr;       // per-instance blocks: launch order, costliest block first
+    int cta_per_sm = 0;         // single-CTA executor: CTAs per SM (0 automatic)
     void *aux = nullptr;        // (c_i, 1 / L_ii) per row, written by the row-block pre-pass
     // packed records of the row-block order (exec_mode 4), built when that mode is chosen
     void *pmeta = nullptr, *pvals = nullptr, *paux = nullptr;
@@ -128,6 +131,8 @@ struct sf_schedule {
     sf_pair pair = SF_TRSV;
     int n = 0;
     int instances = 1;
+    std::vector<int> inst_rows;   // first row of every instance, then n (instances + 1)
+    int *inst_ptr = nullptr;      // the same on the device
     Arena keep;
     DevCsr L, M;
     bool hasM = false;
@@ -300,10 +305,12 @@ sf_status cut_dir(sf_schedule *S, Dir &d, long long C_user, cudaStream_t s, Aren
     return slice_dir(S, d);
 }
 
-// Row-block order of one direction for blocks of B rows (0: automatic, 8192 rows or n).
+// Row-block order of one direction for blocks of B rows (0: automatic, 8192 rows or n; -1: one
+// block per instance, launched costliest first).
 sf_status block_dir(sf_schedule *S, Dir &d, int B, cudaStream_t s, Arena &tmp) {
-    if (B <= 0) B = (int)std::min<long long>(8192, ((long long)S->n + 31) / 32 * 32);
-    const int nb_new = (int)(((long long)S->n + B - 1) / B);
+    const bool per_inst = B < 0;
+    if (B == 0) B = (int)std::min<long long>(8192, ((long long)S->n + 31) / 32 * 32);
+    const int nb_new = per_inst ? S->instances : (int)(((long long)S->n + B - 1) / B);
     if (!d.block_ptr || nb_new > d.nb) {
         d.block_ptr = (int *)S->keep.alloc(sizeof(int) * ((size_t)nb_new + 1));
         d.block_seg = (int *)S->keep.alloc(sizeof(int) * ((size_t)nb_new + 1));
@@ -316,9 +323,30 @@ sf_status block_dir(sf_schedule *S, Dir &d, int B, cudaStream_t s, Arena &tmp) {
     }
     const bool sep = d.kind == K_SEP || d.kind == K_SEP_T;
     cudaError_t e = build_block_order(d.kind, S->n, d.nv, B, d.depth, d.level, sep ? &S->M : nullptr,
-                                      (d.kind == K_SEP_T) ? &S->MT : nullptr, d.border, d.block_ptr, d.seg_ptr,
-                                      d.block_seg, &d.nb, &d.n_segs, &d.max_seg, s, tmp);
+                                      (d.kind == K_SEP_T) ? &S->MT : nullptr, per_inst ? S->inst_ptr : nullptr,
+                                      S->instances, d.border, d.block_ptr, d.seg_ptr, d.block_seg, &d.nb, &d.n_segs,
+                                      &d.max_seg, s, tmp);
     if (e != cudaSuccess) return from_cuda(e, "row-block order");
+    if (per_inst) {
+        // launch order: most level segments first (they bound a CTA's time), then most rows
+        std::vector<int> bs((size_t)d.nb + 1), perm((size_t)d.nb);
+        SF_CK(cudaMemcpyAsync(bs.data(), d.block_seg, sizeof(int) * bs.size(), cudaMemcpyDeviceToHost, s), "block order");
+        SF_CK(cudaStreamSynchronize(s), "block order");
+        for (int b = 0; b < d.nb; ++b) perm[(size_t)b] = b;
+        auto cost = [&](int b) {
+            return (long long)(bs[(size_t)b + 1] - bs[(size_t)b]) * 4096 +
+                   (S->inst_rows[(size_t)b + 1] - S->inst_rows[(size_t)b]);
+        };
+        std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return cost(x) > cost(y); });
+        if (!d.bperm) {
+            d.bperm = (int *)S->keep.alloc(sizeof(int) * (size_t)std::max(d.nb, 1));
+            if (!d.bperm) return fail(SF_ERR_OOM, "inspector: out of device memory");
+        }
+        SF_CK(cudaMemcpyAsync(d.bperm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice, s), "block order");
+        SF_CK(cudaStreamSynchronize(s), "block order");   // perm lives on this stack frame
+        B = 0;
+    }
+    d.per_inst = per_inst;
     if (!d.bdesc) {
         d.bdesc = (int2 *)S->keep.alloc(sizeof(int2) * d.nv);
         if (!d.bdesc) return fail(SF_ERR_OOM, "inspector: out of device memory");
@@ -416,7 +444,7 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
     if (st != SF_OK) return st;
     d.border = (int *)S->keep.alloc(sizeof(int) * nv);
     if (!d.border) return fail(SF_ERR_OOM, "inspector: out of device memory");
-    st = block_dir(S, d, S->block_rows, s, tmp);
+    st = block_dir(S, d, S->exec_mode == 5 ? -1 : S->block_rows, s, tmp);
     if (st != SF_OK) return st;
     d.exec_mode = S->exec_mode;
     d.blpr = d.lpr <= 1 ? 1 : (d.lpr <= 2 ? 2 : (d.lpr <= 16 ? 4 : 32));
@@ -519,7 +547,15 @@ sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
 
 sf_status finish_inspect(sf_schedule *S, const sf_options &o, cudaStream_t s, sf_schedule **out,
                          std::chrono::steady_clock::time_point t0) {
-    sf_status st = build_schedule(S, o, s);
+    // instance boundaries on the device (one instance for sf_inspect)
+    if (S->inst_rows.empty()) S->inst_rows = {0, S->n};
+    S->inst_ptr = (int *)S->keep.alloc(sizeof(int) * S->inst_rows.size());
+    sf_status st = S->inst_ptr ? SF_OK : fail(SF_ERR_OOM, "inspector: out of device memory");
+    if (st == SF_OK && (cudaMemcpyAsync(S->inst_ptr, S->inst_rows.data(), sizeof(int) * S->inst_rows.size(),
+                                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        st = fail(SF_ERR_CUDA, "inspector: instance boundaries");
+    if (st == SF_OK) st = build_schedule(S, o, s);
     if (st != SF_OK) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
@@ -651,12 +687,14 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     if (d.exec_mode == 5) {
         if ((mode != M_TRSV_SPMV && mode != M_TRSV) || k != 1 || a.Lv == nullptr)
             return fail(SF_ERR_UNSUPPORTED, "the single-CTA executor runs SpTRSV -> SpMV and SpTRSV with k = 1");
-        if (d.nb != 1) return fail(SF_ERR_UNSUPPORTED, "the single-CTA executor needs one block holding every row");
+        if (!d.per_inst) return fail(SF_ERR_UNSUPPORTED, "the single-CTA executor needs one block per instance");
         a.order = d.border;
         a.seg_ptr = d.seg_ptr;
         a.block_seg = d.block_seg;
-        cudaError_t e = launch_cta_exec(mode, dtype, S->L.nnz, d.nv, d.n_segs, s, a, d.ev_start, d.ev_stop);
-        if (e == cudaErrorInvalidValue) return fail(SF_ERR_UNSUPPORTED, "x does not fit in one CTA's shared memory");
+        a.block_ptr = d.block_ptr;
+        a.n_blocks = d.nb;
+        const cudaError_t e = launch_cta_exec(mode, dtype, S->inst_ptr, d.bperm, d.cta_per_sm, S->sms, s, a,
+                                              d.ev_start, d.ev_stop);
         if (e != cudaSuccess) return from_cuda(e, "single-CTA executor launch");
         return SF_OK;
     }
@@ -875,6 +913,9 @@ SF_API sf_status sf_inspect_batched(sf_pair pair, int32_t count, const sf_csr *L
     if (!S) return fail(SF_ERR_OOM, "host allocation failed");
     S->n = (int)n;
     S->instances = count;
+    S->inst_rows.resize((size_t)count + 1);
+    for (int t = 0; t < count; ++t) S->inst_rows[(size_t)t] = dl[(size_t)t].row_off;
+    S->inst_rows[(size_t)count] = (int)n;
     Arena tmp;
     auto alloc_csr = [&](DevCsr &d, long long nnz) {
         d.n_rows = d.n_cols = (int)n;
@@ -1274,7 +1315,7 @@ SF_API sf_status sf_schedule_replace(sf_schedule *S, int32_t which, int32_t g2_p
         d.g2 = g2_placement;
         sf_status st = cut_dir(S, d, d.C, s, tmp);
         if (st != SF_OK) return st;
-        st = block_dir(S, d, d.B, s, tmp);
+        st = block_dir(S, d, d.per_inst ? -1 : d.B, s, tmp);
         if (st != SF_OK) return st;
         if (d.exec_mode == 4 && (st = pack_dir(S, d, s)) != SF_OK) return st;
     }
@@ -1290,6 +1331,10 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     if (exec_mode < -1 || exec_mode > 5) return fail(SF_ERR_INVALID_ARG, "exec_mode must be -1 .. 5");
     if (lanes_per_row != 0 && lanes_per_row != 1 && lanes_per_row != 2 && lanes_per_row != 4 && lanes_per_row != 32)
         return fail(SF_ERR_INVALID_ARG, "row-block lanes per row must be 1, 2, 4 or 32");
+    if (exec_mode == 5 && lanes_per_row == 32)
+        return fail(SF_ERR_INVALID_ARG, "single-CTA executor: CTAs per SM must be 1, 2 or 4");
+    if (exec_mode == 5 && block_rows != 0)
+        return fail(SF_ERR_INVALID_ARG, "the single-CTA executor runs whole instances: block_rows must be 0");
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
     cudaStream_t s = (cudaStream_t)stream;
     SF_CK(cudaStreamSynchronize(s), "reblock");
@@ -1297,15 +1342,19 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;
-        if (exec_mode == 5 && !block_rows) block_rows = (int)std::min<long long>(1 << 20, ((long long)S->n + 31) / 32 * 32);
-        if (block_rows && block_rows != dirs[w]->B) {
-            sf_status st = block_dir(S, *dirs[w], block_rows, s, tmp);
+        Dir &d = *dirs[w];
+        // the single-CTA executor takes one block per instance; the row-block executors
+        // blocks of B rows (rebuilt at the automatic size when leaving per-instance blocks)
+        const int B = exec_mode == 5 ? -1 : (block_rows ? block_rows : ((exec_mode >= 2 && d.per_inst) ? 0 : -2));
+        if (B == -1 ? !d.per_inst : (B == 0 || (B > 0 && (B != d.B || d.per_inst)))) {
+            sf_status st = block_dir(S, d, B, s, tmp);
             if (st != SF_OK) return st;
         }
-        if (exec_mode >= 0) dirs[w]->exec_mode = exec_mode;
-        if (lanes_per_row) dirs[w]->blpr = lanes_per_row;
-        if (dirs[w]->exec_mode == 4) {
-            sf_status st = pack_dir(S, *dirs[w], s);
+        if (exec_mode >= 0) d.exec_mode = exec_mode;
+        if (exec_mode == 5) d.cta_per_sm = lanes_per_row;
+        else if (lanes_per_row) d.blpr = lanes_per_row;
+        if (d.exec_mode == 4) {
+            sf_status st = pack_dir(S, d, s);
             if (st != SF_OK) return st;
         }
     }

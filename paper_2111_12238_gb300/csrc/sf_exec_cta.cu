@@ -1,15 +1,20 @@
-// Single-CTA executor for small systems (exec_mode 5, one right-hand side): the whole joint DAG
-// runs on one SM. The CTA first stages into shared memory the right-hand side (as x), the level
-// segments and the vertex order of the row-block order (one block holding every row) and, when
-// they fit as well, L's row pointers, columns and values, with each diagonal entry replaced by
-// its reciprocal. It then walks the segments: the SpTRSV rows of a segment are independent of
-// each other, so the threads take one row each, read the x_j they need from shared memory, and a
-// __syncthreads() separates the segments. Nothing on that dependence chain touches global memory
-// when everything is staged: x_save is written out after the last wavefront, and the
-// second-kernel (SpMV) rows, sinks of the joint DAG, run after it too, every thread on several
-// rows at once with x still in shared memory (their latest placement in the fused order). The
-// intermediate x never leaves the SM: the barrier between wavefronts is a CTA barrier instead of
-// a hand-off through L2. No waits on other CTAs, so nothing to bound.
+// Single-CTA executor (exec_mode 5, one right-hand side): every instance of the system (the
+// whole system for sf_inspect, each independent instance of a block-diagonal batch) runs its
+// joint DAG on one CTA, with no waits on other CTAs. A CTA stages into shared memory what fits
+// of, in this order: the right-hand side (as x), the level segments and vertex order of its
+// block of the row-block order (one block per instance), and L's row pointers, columns and
+// values with each diagonal entry replaced by its reciprocal. What does not fit is read from
+// global memory, x then living in the output buffer. The CTA walks its segments: the SpTRSV rows
+// of a segment are independent of each other, so the threads take one row each, read the x_j
+// they need, and a barrier of those threads separates the segments. With everything staged,
+// nothing on that dependence chain touches global memory. For SpTRSV -> SpMV a quarter of the
+// warps run the second kernel's rows instead, concurrently with the solve: a row of segment g
+// waits (in shared memory) until the solver threads have finished the segments before g, then
+// reads M from global memory and x on chip, so M's loads overlap the solve rather than
+// following it. x_save is written out after the last wavefront. The intermediate x never leaves
+// the SM: the barrier between wavefronts is a CTA barrier instead of a hand-off through L2.
+// Blocks are launched costliest first (most segments), so that the long instances start in the
+// first wave of a batch. The only wait, on the solver's progress counter, is bounded.
 #include <algorithm>
 #include <atomic>
 
@@ -19,16 +24,28 @@ namespace sf {
 
 namespace {
 
-constexpr int kCtaThreads = 1024;
-constexpr int kStageUnroll = 8;   // independent loads in flight per thread while staging
+constexpr int kCtaMaxThreads = 1024;
+constexpr int kStageUnroll = 8;    // independent loads in flight per thread while staging
 constexpr int kMaxDevices = 64;
-constexpr int kRowsInFlight = 4;   // SpMV rows a thread works on together after the solve
+constexpr size_t kCtlBytes = 16;   // progress counter of the solver threads, ahead of the layout
+constexpr int kSpmvPrefetch = 8;   // entries of an SpMV row loaded before its wait
 
-__device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+__device__ __forceinline__ unsigned ld_relaxed_cta_shared(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta_shared(unsigned *p, unsigned v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+// barrier 1 among the first `count` threads (a multiple of 32) of the CTA
+__device__ __forceinline__ void solver_barrier(int count) { asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory"); }
 
-// Copies n elements from global to shared memory with kStageUnroll loads in flight per thread.
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// dst[i] = src[i] - shift for i < n, with kStageUnroll loads in flight per thread.
 template <typename E>
-__device__ __forceinline__ void stage(E *__restrict__ dst, const E *__restrict__ src, long long n) {
+__device__ __forceinline__ void stage(E *__restrict__ dst, const E *__restrict__ src, long long n, E shift = E(0)) {
     for (long long base = threadIdx.x; base < n; base += (long long)kStageUnroll * blockDim.x) {
         E v[kStageUnroll];
 #pragma unroll
@@ -39,161 +56,217 @@ __device__ __forceinline__ void stage(E *__restrict__ dst, const E *__restrict__
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
             const long long e = base + (long long)u * blockDim.x;
-            if (e < n) dst[e] = v[u];
+            if (e < n) dst[e] = v[u] - shift;
         }
     }
 }
 
-// Shared-memory layout, each part 16-byte aligned: x[n] (T); when OS: segment pointers
-// [segs + 1] and the vertex order [nv] (int); when LS: L values [nnz] (T, the diagonal entry of
-// each row replaced by its reciprocal), L columns [nnz] (int), L row pointers [n + 1] (int).
-template <typename T, bool OS, bool LS>
-__global__ void __launch_bounds__(kCtaThreads, 1)
-    k_cta_exec(const ExecArgs a, int mode, long long nnzL, long long nv, int segs) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = a.n;
+// One block (instance): rows [r0, r1), positions [p0, p1) of the order, segments [s0, s1),
+// L entries [e0, e1). LV: 0 nothing staged (x in the output buffer), 1 x, 2 x and the order,
+// 3 x, the order and L. Shared-memory layout after the kCtlBytes control word, each part
+// 16-byte aligned: x[r1 - r0] (T), segment pointers [s1 - s0 + 1], order [p1 - p0], L values
+// [e1 - e0] (T), L columns [e1 - e0] (relative to r0), L row pointers [r1 - r0 + 1] (relative
+// to e0).
+template <typename T, int LV>
+__device__ void cta_block(const ExecArgs &a, int mode, int r0, int r1, int p0, int p1, int s0, int s1, int e0, int e1,
+                          unsigned char *smem_all) {
+    const int nr = r1 - r0;
+    const int ne = e1 - e0;
+    T *xg = mode == M_TRSV ? (T *)a.y : (T *)a.xs;   // x in global memory (the output)
+    unsigned *done = (unsigned *)smem_all;           // segments the solver threads have finished
+    unsigned char *smem = smem_all + kCtlBytes;
     size_t off = 0;
-    T *x = (T *)smem;
-    off = align16(sizeof(T) * (size_t)n);
-    int *s_seg = (int *)(smem + off);
-    if (OS) off += align16(sizeof(int) * ((size_t)segs + 1));
-    int *s_order = (int *)(smem + off);
-    if (OS) off += align16(sizeof(int) * (size_t)nv);
-    T *s_lv = (T *)(smem + off);
-    if (LS) off += align16(sizeof(T) * (size_t)nnzL);
-    int *s_lc = (int *)(smem + off);
-    if (LS) off += align16(sizeof(int) * (size_t)nnzL);
-    int *s_lrp = (int *)(smem + off);
+    T *sx = (T *)smem;
+    off += align16(sizeof(T) * (size_t)nr);
+    int *sseg = (int *)(smem + off);
+    off += align16(sizeof(int) * ((size_t)(s1 - s0) + 1));
+    int *sord = (int *)(smem + off);
+    off += align16(sizeof(int) * (size_t)(p1 - p0));
+    T *slv = (T *)(smem + off);
+    off += align16(sizeof(T) * (size_t)ne);
+    int *slc = (int *)(smem + off);
+    off += align16(sizeof(int) * (size_t)ne);
+    int *srp = (int *)(smem + off);
     const T *Lv = (const T *)a.Lv;
-    if constexpr (OS) {
-        stage<int>(s_seg, a.seg_ptr, (long long)segs + 1);
-        stage<int>(s_order, a.order, nv);
+    const T *b = (const T *)a.b;
+    if constexpr (LV >= 2) {
+        stage<int>(sseg, a.seg_ptr + s0, (long long)(s1 - s0) + 1);
+        stage<int>(sord, a.order + p0, p1 - p0);
     }
-    if constexpr (LS) {
-        stage<T>(s_lv, Lv, nnzL);
-        stage<int>(s_lc, a.Lci, nnzL);
-        stage<int>(s_lrp, a.Lrp, (long long)n + 1);
+    if constexpr (LV >= 3) {
+        stage<T>(slv, Lv + e0, ne);
+        stage<int>(slc, a.Lci + e0, ne, r0);
+        stage<int>(srp, a.Lrp + r0, (long long)nr + 1, e0);
     }
     // x starts as b (a row then subtracts its sum in place and scales)
-    stage<T>(x, (const T *)a.b, n);
+    if constexpr (LV >= 1) stage<T>(sx, b + r0, nr);
+    else
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) xg[r0 + i] = __ldg(b + r0 + i);
+    if (threadIdx.x == 0) *done = 0u;
     __syncthreads();
-    if constexpr (LS) {
+    if constexpr (LV >= 3) {
         // diagonal entries to reciprocals, off the dependence chain
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int dg = s_lrp[i + 1] - 1;
-            const T d = s_lv[dg];
-            if (d == T(0)) record_error(a.st, SF_ERR_NONFINITE, i);
-            s_lv[dg] = T(1) / d;
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+            const int dg = srp[i + 1] - 1;
+            const T d = slv[dg];
+            if (d == T(0)) record_error(a.st, SF_ERR_NONFINITE, r0 + i);
+            slv[dg] = T(1) / d;
         }
         __syncthreads();
     }
-    const int *seg = OS ? s_seg : a.seg_ptr;
-    const int *ord = OS ? s_order : a.order;
-    const int *rp = LS ? s_lrp : a.Lrp;
-    const int *ci = LS ? s_lc : a.Lci;
-    const T *lv = LS ? s_lv : Lv;
-    for (int g = 0; g < segs; ++g) {
-        const int q0 = seg[g], q1 = seg[g + 1];
-        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-            const unsigned o = (unsigned)ord[q];
-            if (o >> 31) continue;   // SpMV row: after the last wavefront
-            // SpTRSV row: x_i = (b_i - sum_{j<i} L_ij x_j) / L_ii
-            const int row = (int)o;
-            const int rs = rp[row], dg = rp[row + 1] - 1;
-            T acc = T(0);
-            for (int e = rs; e < dg; ++e) acc += lv[e] * x[ci[e]];
-            if constexpr (LS) {
-                x[row] = (x[row] - acc) * lv[dg];
-            } else {
-                const T d = lv[dg];
-                if (d == T(0)) record_error(a.st, SF_ERR_NONFINITE, row);
-                x[row] = (x[row] - acc) / d;
+    // solver threads: the SpTRSV rows; for SpTRSV -> SpMV the last quarter of the warps run the
+    // SpMV rows concurrently
+    const int ns = mode == M_TRSV_SPMV ? (int)blockDim.x - (int)blockDim.x / 4 : (int)blockDim.x;
+    const int tid = threadIdx.x;
+    if (tid < ns) {
+        for (int g = s0; g < s1; ++g) {
+            const int q0 = LV >= 2 ? sseg[g - s0] : a.seg_ptr[g];
+            const int q1 = LV >= 2 ? sseg[g - s0 + 1] : a.seg_ptr[g + 1];
+            for (int q = q0 + tid; q < q1; q += ns) {
+                const unsigned o = (unsigned)(LV >= 2 ? sord[q - p0] : a.order[q]);
+                if (o >> 31) continue;   // SpMV row
+                // SpTRSV row: x_i = (b_i - sum_{j<i} L_ij x_j) / L_ii
+                const int row = (int)o;
+                if constexpr (LV >= 3) {
+                    const int li = row - r0;
+                    const int rs = srp[li], dg = srp[li + 1] - 1;
+                    T acc = T(0);
+                    for (int e = rs; e < dg; ++e) acc += slv[e] * sx[slc[e]];
+                    sx[li] = (sx[li] - acc) * slv[dg];
+                } else {
+                    const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+                    T acc = T(0);
+                    for (int e = rs; e < dg; ++e) {
+                        const int j = __ldg(a.Lci + e);
+                        acc += __ldg(Lv + e) * (LV >= 1 ? sx[j - r0] : xg[j]);
+                    }
+                    const T d = __ldg(Lv + dg);
+                    if (d == T(0)) record_error(a.st, SF_ERR_NONFINITE, row);
+                    if constexpr (LV >= 1) sx[row - r0] = (sx[row - r0] - acc) / d;
+                    else xg[row] = (xg[row] - acc) / d;
+                }
             }
+            solver_barrier(ns);
+            if (tid == 0) st_release_cta_shared(done, (unsigned)(g - s0 + 1));
         }
-        __syncthreads();
+    } else {
+        // SpMV rows: y_i = sum_j M_ij x_j. Each thread takes every nsp-th position of the block;
+        // a row's pattern and first kSpmvPrefetch values are loaded before it waits until the
+        // segments before its own are done, so only the on-chip x reads follow the wait.
+        const int nsp = (int)blockDim.x - ns, st = tid - ns;
+        const T *Mv = (const T *)a.Mv;
+        T *y = (T *)a.y;
+        constexpr int P = kSpmvPrefetch;
+        int g = s0;             // segment of position q (q only grows)
+        unsigned seen = 0;      // segments known to be done
+        unsigned long long t0 = 0;
+        for (int q = p0 + st; q < p1; q += nsp) {
+            const unsigned o = (unsigned)(LV >= 2 ? sord[q - p0] : a.order[q]);
+            if (!(o >> 31)) continue;
+            while ((LV >= 2 ? sseg[g + 1 - s0] : a.seg_ptr[g + 1]) <= q) ++g;
+            const int row = (int)(o & 0x7fffffffu);
+            const int ms = __ldg(a.Mrp + row), me = __ldg(a.Mrp + row + 1);
+            int jc[P];
+            T mv[P];
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                jc[u] = ms + u < me ? __ldg(a.Mci + ms + u) : r0;
+                mv[u] = ms + u < me ? __ldg(Mv + ms + u) : T(0);
+            }
+            if (seen < (unsigned)(g - s0)) {
+                // poll with a short sleep (the solver warps keep the issue slots), then acquire
+                bool ok = true;
+                for (unsigned it = 0; (seen = ld_relaxed_cta_shared(done)) < (unsigned)(g - s0); ++it) {
+                    __nanosleep(64);
+                    if ((it & 15u) == 15u) {
+                        const unsigned long long now = global_ns();
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > a.timeout_ns) {
+                            record_error(a.st, SF_ERR_TIMEOUT, row);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                if (!ok) break;
+                asm volatile("fence.acq_rel.cta;" ::: "memory");
+                t0 = 0;
+            }
+            T acc = T(0);
+#pragma unroll
+            for (int u = 0; u < P; ++u)
+                if (ms + u < me) acc += mv[u] * (LV >= 1 ? sx[jc[u] - r0] : xg[jc[u]]);
+            for (int e = ms + P; e < me; ++e) {
+                const int j = __ldg(a.Mci + e);
+                acc += __ldg(Mv + e) * (LV >= 1 ? sx[j - r0] : xg[j]);
+            }
+            y[row] = acc;
+        }
     }
-    T *out_x = mode == M_TRSV ? (T *)a.y : (T *)a.xs;
-    if (out_x)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) out_x[i] = x[i];
-    if (mode != M_TRSV_SPMV) return;
-    // y = M x: kRowsInFlight rows per thread at a time, their entries loaded together
-    constexpr int R = kRowsInFlight;
-    const T *Mv = (const T *)a.Mv;
-    T *y = (T *)a.y;
-    for (int i0 = threadIdx.x; i0 < n; i0 += R * blockDim.x) {
-        int ms[R], me[R];
-        int len = 0;
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-            const int i = i0 + u * blockDim.x;
-            ms[u] = i < n ? __ldg(a.Mrp + i) : 0;
-            me[u] = i < n ? __ldg(a.Mrp + i + 1) : 0;
-            len = max(len, me[u] - ms[u]);
-        }
-        T acc[R];
-#pragma unroll
-        for (int u = 0; u < R; ++u) acc[u] = T(0);
-        for (int t = 0; t < len; ++t) {
-#pragma unroll
-            for (int u = 0; u < R; ++u)
-                if (ms[u] + t < me[u]) acc[u] += __ldg(Mv + ms[u] + t) * x[__ldg(a.Mci + ms[u] + t)];
-        }
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-            const int i = i0 + u * blockDim.x;
-            if (i < n) y[i] = acc[u];
-        }
-    }
+    __syncthreads();
+    if constexpr (LV >= 1)
+        for (int i = tid; i < nr; i += blockDim.x) xg[r0 + i] = sx[i];
 }
 
-size_t bytes_x(size_t es, int n) { return (es * (size_t)n + 15) & ~(size_t)15; }
-size_t bytes_order(long long nv, int segs) {
-    return ((4 * ((size_t)segs + 1) + 15) & ~(size_t)15) + ((4 * (size_t)nv + 15) & ~(size_t)15);
-}
-size_t bytes_L(size_t es, int n, long long nnzL) {
-    return ((es * (size_t)nnzL + 15) & ~(size_t)15) + ((4 * (size_t)nnzL + 15) & ~(size_t)15) +
-           ((4 * ((size_t)n + 1) + 15) & ~(size_t)15);
-}
-
+// One CTA per block of the per-instance row-block order (block bperm[blockIdx.x]); `budget`
+// bytes of dynamic shared memory decide what the block stages.
 template <typename T>
-const void *cta_kernel(bool os, bool ls) {
-    if (os) return ls ? (const void *)k_cta_exec<T, true, true> : (const void *)k_cta_exec<T, true, false>;
-    return ls ? (const void *)k_cta_exec<T, false, true> : (const void *)k_cta_exec<T, false, false>;
+__global__ void __launch_bounds__(kCtaMaxThreads, 1)
+    k_cta_exec(const ExecArgs a, int mode, const int *__restrict__ inst_ptr, const int *__restrict__ bperm,
+               unsigned budget) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int blk = bperm ? __ldg(bperm + blockIdx.x) : (int)blockIdx.x;
+    const int r0 = __ldg(inst_ptr + blk), r1 = __ldg(inst_ptr + blk + 1);
+    const int p0 = __ldg(a.block_ptr + blk), p1 = __ldg(a.block_ptr + blk + 1);
+    const int s0 = __ldg(a.block_seg + blk), s1 = __ldg(a.block_seg + blk + 1);
+    const int e0 = __ldg(a.Lrp + r0), e1 = __ldg(a.Lrp + r1);
+    const size_t nr = (size_t)(r1 - r0), ne = (size_t)(e1 - e0);
+    if (budget < kCtlBytes) return;   // the launcher never asks for less
+    const size_t need1 = kCtlBytes + align16(sizeof(T) * nr);
+    const size_t need2 = need1 + align16(sizeof(int) * ((size_t)(s1 - s0) + 1)) + align16(sizeof(int) * (size_t)(p1 - p0));
+    const size_t need3 = need2 + align16(sizeof(T) * ne) + align16(sizeof(int) * ne) + align16(sizeof(int) * (nr + 1));
+    if (need3 <= budget) cta_block<T, 3>(a, mode, r0, r1, p0, p1, s0, s1, e0, e1, smem);
+    else if (need2 <= budget) cta_block<T, 2>(a, mode, r0, r1, p0, p1, s0, s1, e0, e1, smem);
+    else if (need1 <= budget) cta_block<T, 1>(a, mode, r0, r1, p0, p1, s0, s1, e0, e1, smem);
+    else cta_block<T, 0>(a, mode, r0, r1, p0, p1, s0, s1, e0, e1, smem);
 }
 
 }  // namespace
 
-// Launches the single-CTA executor. Shared memory holds x, then (when they fit) the segments and
-// the order, then (when they fit too) L; what does not fit is read from global memory.
-// cudaErrorInvalidValue when x alone does not fit.
-cudaError_t launch_cta_exec(int mode, int dtype, long long nnzL, long long nv, int segs, cudaStream_t s,
-                            const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
-    int dev = 0, smax = 0;
+// Launches the single-CTA executor over the a.n_blocks blocks of the per-instance order:
+// cta_per_sm CTAs of 1024 / cta_per_sm threads share an SM (0: one when the blocks fit in one
+// wave, else two), each with an equal share of the SM's shared memory.
+cudaError_t launch_cta_exec(int mode, int dtype, const int *inst_ptr, const int *bperm, int cta_per_sm, int sms,
+                            cudaStream_t s, const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
+    int dev = 0, smax = 0, ssm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t es = dtype == 0 ? 8 : 4;
-    size_t smem = bytes_x(es, a.n);
-    if (smem > (size_t)smax) return cudaErrorInvalidValue;
-    const bool os = smem + bytes_order(nv, segs) <= (size_t)smax;
-    if (os) smem += bytes_order(nv, segs);
-    const bool ls = smem + bytes_L(es, a.n, nnzL) <= (size_t)smax;
-    if (ls) smem += bytes_L(es, a.n, nnzL);
-    const void *f = dtype == 0 ? cta_kernel<double>(os, ls) : cta_kernel<float>(os, ls);
+    cudaDeviceGetAttribute(&ssm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int cps = cta_per_sm > 0 ? cta_per_sm : (a.n_blocks > sms ? 2 : 1);
+    const int threads = kCtaMaxThreads / cps;
+    // 1 KB of each CTA's shared memory is reserved by the system
+    const int budget = (int)(std::min<long long>(smax, (long long)ssm / cps - 1024) & ~15LL);
+    if (budget < 16) return cudaErrorInvalidValue;
+    const void *f = dtype == 0 ? (const void *)k_cta_exec<double> : (const void *)k_cta_exec<float>;
     // the opt-in shared-memory size is set once per device and kernel to the largest request
-    static std::atomic<int> opted[kMaxDevices][2][2][2];
+    static std::atomic<int> opted[kMaxDevices][2];
     cudaError_t e = cudaSuccess;
-    if (dev >= kMaxDevices || opted[dev][dtype][os][ls].load() < (int)smem) {
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= kMaxDevices || opted[dev][dtype].load() < budget) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, budget);
         if (e != cudaSuccess) return e;
         if (dev < kMaxDevices) {
-            int cur = opted[dev][dtype][os][ls].load();
-            while (cur < (int)smem && !opted[dev][dtype][os][ls].compare_exchange_weak(cur, (int)smem)) {
+            int cur = opted[dev][dtype].load();
+            while (cur < budget && !opted[dev][dtype].compare_exchange_weak(cur, budget)) {
             }
         }
     }
-    void *args[] = {(void *)&a, (void *)&mode, (void *)&nnzL, (void *)&nv, (void *)&segs};
+    unsigned ub = (unsigned)budget;
+    void *args[] = {(void *)&a, (void *)&mode, (void *)&inst_ptr, (void *)&bperm, (void *)&ub};
     if (ev_start && (e = cudaEventRecord(ev_start, s)) != cudaSuccess) return e;
-    if ((e = cudaLaunchKernel(f, dim3(1), dim3(kCtaThreads), args, smem, s)) != cudaSuccess) return e;
+    if (a.n_blocks > 0 &&
+        (e = cudaLaunchKernel(f, dim3((unsigned)a.n_blocks), dim3((unsigned)threads), args, (size_t)budget, s)) !=
+            cudaSuccess)
+        return e;
     if (ev_stop) return cudaEventRecord(ev_stop, s);
     return cudaSuccess;
 }

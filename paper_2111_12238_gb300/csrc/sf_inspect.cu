@@ -743,18 +743,34 @@ cudaError_t split_partition_classes(int P, const int *part_ptr, const int *order
 }
 
 // ------------------------------------------------------------------------------ row blocks
+// Instance of row i: the t with inst_ptr[t] <= i < inst_ptr[t + 1].
+__device__ __forceinline__ int instance_of(int i, const int *__restrict__ inst_ptr, int n_inst) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst_ptr[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Block of every vertex for the row-block executor: first-kernel rows by their own row
 // (decreasing row order for the transposed kinds), second-kernel rows by the latest block
 // among the rows they read (columns ascend, so that is the last column of an M row, or the
-// first row of an A^T row when blocks run in decreasing row order). key = block*depth+level.
+// first row of an A^T row when blocks run in decreasing row order). With inst_ptr, the blocks
+// are the independent instances of a block-diagonal system instead, every vertex in the block
+// of its row's instance. key = block*depth+level.
 __global__ void k_block_keys(int kind, int n, long long nv, int B, int nb, int depth, const int *__restrict__ level,
                              const int *__restrict__ Mrp, const int *__restrict__ Mci,
                              const int *__restrict__ MTrp, const int *__restrict__ MTci,
-                             unsigned *__restrict__ keys, unsigned *__restrict__ vals, int *__restrict__ bcount) {
+                             const int *__restrict__ inst_ptr, unsigned *__restrict__ keys,
+                             unsigned *__restrict__ vals, int *__restrict__ bcount) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
         const bool rev = kind == K_PAIRED_T || kind == K_SEP_T;
         long long b;
-        if (v < n) {
+        if (inst_ptr) {
+            b = instance_of((int)(v < n ? v : v - n), inst_ptr, nb);
+        } else if (v < n) {
             b = rev ? nb - 1 - v / B : v / B;
         } else {
             const int i = (int)(v - n);
@@ -807,9 +823,11 @@ __global__ void k_block_seg(int nb, long long nv, const int *__restrict__ block_
 }
 
 cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, const int *level, const DevCsr *M,
-                              const DevCsrT *MT, int *order, int *block_ptr, int *seg_ptr, int *block_seg,
-                              int *nb_out, int *n_segs_out, int *max_width_out, cudaStream_t s, Arena &ar) {
-    const int nb = (int)((n + (long long)B - 1) / B);
+                              const DevCsrT *MT, const int *inst_ptr, int n_inst, int *order, int *block_ptr,
+                              int *seg_ptr, int *block_seg, int *nb_out, int *n_segs_out, int *max_width_out,
+                              cudaStream_t s, Arena &ar) {
+    const int nb = inst_ptr ? n_inst : (int)((n + (long long)B - 1) / B);
+    if ((unsigned long long)nb * (unsigned long long)std::max(depth, 1) > 0xffffffffull) return cudaErrorInvalidValue;
     unsigned *keys = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
     unsigned *vals = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
     int *cnt = (int *)ar.alloc(sizeof(int) * ((size_t)nb + 1));
@@ -821,7 +839,7 @@ cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, c
     cudaMemsetAsync(out2, 0, sizeof(int) * 2, s);
     k_block_keys<<<grid_for(nv, 256, 4096), 256, 0, s>>>(kind, n, nv, B, nb, depth, level, M ? M->rowptr : nullptr,
                                                          M ? M->colidx : nullptr, MT ? MT->t.rowptr : nullptr,
-                                                         MT ? MT->t.colidx : nullptr, keys, vals, cnt);
+                                                         MT ? MT->t.colidx : nullptr, inst_ptr, keys, vals, cnt);
     cudaError_t e = radix_sort_pairs(keys, vals, nv, bits_for((unsigned long long)nb * depth - 1), s, ar);
     if (e != cudaSuccess) return e;
     k_encode_order<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, n, vals, order);

@@ -85,9 +85,12 @@ cudaError_t build_ic0_pairs(const DevCsr &L, long long max_pairs, int **pp_out, 
                             cudaStream_t s, Arena &ar, Arena &keep);
 cudaError_t split_partition_classes(int P, const int *part_ptr, const int *order, int *plist, int *n_class0,
                                     cudaStream_t s, Arena &ar);
+// Row-block order: blocks of B rows, or (inst_ptr != NULL) one block per instance of a
+// block-diagonal system, inst_ptr[0..n_inst] being the instances' first rows.
 cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, const int *level, const DevCsr *M,
-                              const DevCsrT *MT, int *order, int *block_ptr, int *seg_ptr, int *block_seg,
-                              int *nb_out, int *n_segs_out, int *max_width_out, cudaStream_t s, Arena &ar);
+                              const DevCsrT *MT, const int *inst_ptr, int n_inst, int *order, int *block_ptr,
+                              int *seg_ptr, int *block_seg, int *nb_out, int *n_segs_out, int *max_width_out,
+                              cudaStream_t s, Arena &ar);
 cudaError_t build_block_desc(int kind, long long nv, const int *order, const DevCsr &L, const DevCsr *M,
                              const DevCsrT &LT, const DevCsrT *MT, int2 *desc, cudaStream_t s);
 cudaError_t concat_patterns(const std::vector<InstDesc> &h, int *rp_out, int *ci_out, long long total_nnz,

@@ -138,11 +138,11 @@ cudaError_t launch_rdiag(int dtype, int n, int k, const int *Lrp, const void *Lv
 cudaError_t launch_exec_next(int mode, int dtype, int lpr, bool vf, int team, int minb, int blocks, cudaStream_t s,
                              const ExecArgs &a);
 int occupancy_next(int mode, int dtype, int lpr, bool vf, int team, int minb);
-// Single-CTA executor (exec_mode 5, k = 1): the row-block order with one block holding every row
-// (a.order of nv vertices, a.seg_ptr of segs segments, a.block_seg), staged in shared memory
-// with x and, when it fits as well, L. cudaErrorInvalidValue when x alone does not fit.
-cudaError_t launch_cta_exec(int mode, int dtype, long long nnzL, long long nv, int segs, cudaStream_t s,
-                            const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop);
+// Single-CTA executor (exec_mode 5, k = 1): one CTA per block of the per-instance row-block
+// order (a.order, a.seg_ptr, a.block_ptr, a.block_seg, a.n_blocks; inst_ptr the instances'
+// first rows; bperm the launch order of the blocks), cta_per_sm CTAs per SM (0 automatic).
+cudaError_t launch_cta_exec(int mode, int dtype, const int *inst_ptr, const int *bperm, int cta_per_sm, int sms,
+                            cudaStream_t s, const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop);
 constexpr int kIluMaxRow = 256;   // longest row of A an ILU0 row keeps on chip
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team, int minb);

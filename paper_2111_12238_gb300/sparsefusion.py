@@ -292,7 +292,8 @@ class Schedule:
 
     def reblock(self, which=-1, block_rows=0, exec_mode=-1, lanes_per_row=0, stream=None):
         """Rebuilds the row-block order for `block_rows` rows per block and/or selects the
-        executor (exec_mode 0 automatic, 1 partitions, 2-4 row blocks, 5 single CTA)."""
+        executor (exec_mode 0 automatic, 1 partitions, 2-4 row blocks, 5 one CTA per instance;
+        for 5, block_rows must be 0 and lanes_per_row is the number of CTAs per SM)."""
         _check(load_library().sf_schedule_reblock(self.handle, int(which), int(block_rows), int(exec_mode),
                                                   int(lanes_per_row), _stream(stream)), "sf_schedule_reblock")
 

@@ -10,8 +10,9 @@ from paper_2111_12238_gb300 import sparsefusion as sf
 
 
 class FakeSched:
-    def __init__(self, pair="trsv_spmv", separated=True, n=5000, tma_fails=False):
+    def __init__(self, pair="trsv_spmv", separated=True, n=5000, tma_fails=False, instances=1):
         self.pair, self.separated, self.n, self.tma_fails = pair, separated, n, tma_fails
+        self.instances = instances
         self.state = dict(exec="partitions", C=0, lanes=0, team=0, g2=0, occ=1, split=0, B=0, blanes=0, rt=0,
                           slices=0)
 
@@ -21,7 +22,7 @@ class FakeSched:
         units = nv + 50 if 0 < self.state["slices"] < 100 else 0
         return dict(n_items=nv, adj_n_items=0, cost_total=4 * nv, adj_cost_total=0, n=self.n,
                     parts_class0=7 if self.separated else 0, adj_parts_class0=0, depth=50, adj_depth=0,
-                    instances=1, slice_units=units, adj_slice_units=0)
+                    instances=self.instances, slice_units=units, adj_slice_units=0)
 
     def replace(self, which, g2):
         self.state["g2"] = g2
@@ -32,8 +33,11 @@ class FakeSched:
     def reblock(self, which, B, mode, lanes):
         if mode == 4 and self.tma_fails:
             raise sf.SparseFusionError(8, "sf_schedule_reblock", "does not fit")
-        if mode in (2, 3, 4, 5):
-            self.state.update(exec={2: "blocks", 3: "ws", 4: "tma", 5: "cta"}[mode], B=B, blanes=lanes)
+        if mode == 5:
+            assert B == 0
+            self.state.update(exec="cta", B=0, cps=lanes)
+        elif mode in (2, 3, 4):
+            self.state.update(exec={2: "blocks", 3: "ws", 4: "tma"}[mode], B=B, blanes=lanes)
         else:
             self.state["exec"] = "partitions"
 
@@ -133,3 +137,18 @@ def test_row_block_sizes_that_do_not_fit_are_skipped(fake_timing):
     r = autotune.tune(s, lambda: None, k=1, budget_s=60, use_cache=False)
     assert "tma" not in {t["exec"] for t in r["trials"]}
     assert r["exec"] == "partitions"
+
+
+def test_batches_try_the_single_cta_executor_at_each_sm_share(fake_timing):
+    # a batch of large instances: one CTA per instance at 2, 1 and 4 CTAs per SM, right after
+    # the first partition shape; a single large system does not try it
+    s = FakeSched(n=2_000_000, instances=512)
+    fake_timing["sched"] = s
+    r = autotune.tune(s, lambda: None, k=1, budget_s=60, use_cache=False)
+    cta = [t for t in r["trials"] if t["exec"] == "cta"]
+    assert [t["cps"] for t in cta[:3]] == [2, 1, 4]
+    assert r["trials"][0]["exec"] == "partitions" and r["trials"][1]["exec"] == "cta"
+    s1 = FakeSched(n=2_000_000)
+    fake_timing["sched"] = s1
+    r1 = autotune.tune(s1, lambda: None, k=1, budget_s=60, use_cache=False)
+    assert not any(t["exec"] == "cta" for t in r1["trials"])

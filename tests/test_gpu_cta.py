@@ -1,8 +1,10 @@
-"""Single-CTA executor (exec_mode 5, k = 1): the whole joint DAG of a small SpTRSV -> SpMV (or
-SpTRSV alone) runs in one CTA with x in shared memory and one CTA barrier per level segment.
-Results match the FP64 oracle for both element types, with L staged in shared memory and
-read from global memory when it does not fit; exact integer systems match bit for bit; what
-it does not serve is refused with SF_ERR_UNSUPPORTED before anything runs."""
+"""Single-CTA executor (exec_mode 5, k = 1): the joint DAG of a SpTRSV -> SpMV (or SpTRSV alone)
+runs on one CTA per instance (the whole system, or each instance of a batch) with one CTA
+barrier per level segment and x, the order and L in shared memory as far as they fit. Results
+match the FP64 oracle for both element types whatever is staged (everything, x and the order,
+x alone, nothing); exact integer systems match bit for bit; the per-instance block order is the
+(instance, level, vertex) sort of the oracle's levels; what the executor does not serve is
+refused before anything runs."""
 import numpy as np
 import pytest
 import torch
@@ -12,9 +14,10 @@ from paper_2111_12238_gb300 import inputs as I
 from paper_2111_12238_gb300 import sparsefusion as sf
 from tests._gpu import TOL, col_rel_err, dev_csr, host, need_cuda, t
 
-pytestmark = pytest.mark.gpu
-
 UNSUPPORTED = 8
+INVALID_ARG = 1
+
+pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -99,15 +102,96 @@ def test_refusals():
     with pytest.raises(sf.SparseFusionError) as ei:
         sch.adjoint(Lv, Mv, t(w.gy), saved=xs)
     assert ei.value.status == UNSUPPORTED
-    # x larger than one CTA's shared memory (40000 doubles); the same system in FP32 fits
+    # whole instances only: no block size, and 1, 2 or 4 CTAs per SM
+    with pytest.raises(sf.SparseFusionError) as ei:
+        sch.reblock(0, 512, 5, 0)
+    assert ei.value.status == INVALID_ARG
+    with pytest.raises(sf.SparseFusionError) as ei:
+        sch.reblock(0, 0, 5, 32)
+    assert ei.value.status == INVALID_ARG
+
+
+def test_x_larger_than_shared_memory():
+    # 40000 doubles do not fit in one CTA's shared memory: x lives in the output buffer; the
+    # same system in FP32 keeps x on chip
+    need_cuda()
     n = 40000
     L = I.powerlaw_lower(n, 3, 20, 86)
     b = I.dense_vectors(n, 1, 87, I.S_RHS)
-    s2 = sf.inspect("trsv", dev_csr(L))
-    s2.reblock(0, 0, 5, 0)
-    with pytest.raises(sf.SparseFusionError) as ei:
-        s2.execute(t(L.vals), b=t(b))
-    assert ei.value.status == UNSUPPORTED
-    x = s2.execute(t(L.vals, torch.float32), b=t(b, torch.float32))
-    s2.check()
-    assert col_rel_err(host(x), oracle.trsv_lower(L, b)) < TOL[torch.float32]
+    x_ref = oracle.trsv_lower(L, b)
+    sch = sf.inspect("trsv", dev_csr(L))
+    sch.reblock(0, 0, 5, 0)
+    for dtype in (torch.float64, torch.float32):
+        x = sch.execute(t(L.vals, dtype), b=t(b, dtype))
+        sch.check()
+        assert col_rel_err(host(x), x_ref) < TOL[dtype]
+
+
+def _blockdiag(mats):
+    n = sum(m.n_rows for m in mats)
+    rp, ci, vals, off, eoff = [np.zeros(1, np.int32)], [], [], 0, 0
+    for m in mats:
+        rp.append((m.rowptr[1:] + eoff).astype(np.int32))
+        ci.append((m.colidx + off).astype(np.int32))
+        vals.append(m.vals)
+        off += m.n_rows
+        eoff += int(m.rowptr[-1])
+    return I.Csr(n, n, np.concatenate(rp), np.concatenate(ci), np.concatenate(vals))
+
+
+@pytest.mark.parametrize("cps", [1, 2, 4])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_one_cta_per_instance(cps, dtype):
+    # instance sizes 300 .. 40000: at 4 CTAs per SM (56 KB each) the large ones keep nothing on
+    # chip, at 1 CTA per SM the small ones stage everything
+    need_cuda()
+    w = I.batched_trsv_spmv(count=24, nmin=300, nmax=40000, seed=12)
+    sch = sf.inspect_batched("trsv_spmv", [dev_csr(x.L) for x in w.instances], [dev_csr(x.M) for x in w.instances])
+    sch.reblock(0, 0, 5, cps)
+    inf = sch.info()
+    assert inf["exec_mode"] == 5 and inf["n_blocks"] == 24
+    assert sch.launches(0, 1) == 1
+    Lv = t(np.concatenate([x.L.vals for x in w.instances]), dtype)
+    Mv = t(np.concatenate([x.M.vals for x in w.instances]), dtype)
+    b = t(w.b, dtype)
+    xs = torch.empty_like(b)
+    y = sch.execute(Lv, Mv, b=b, x_save=xs)
+    sch.check()
+    off = 0
+    for x in w.instances:
+        xr, yr = oracle.trsv_spmv(x.L, x.M, x.b)
+        assert col_rel_err(host(xs)[off:off + x.n], xr) < TOL[dtype]
+        assert col_rel_err(host(y)[off:off + x.n], yr) < TOL[dtype]
+        off += x.n
+    # back to the row-block executor at its automatic size, then to the partitions
+    sch.reblock(0, 0, 3, 0)
+    B = min(8192, -(-w.n // 32) * 32)
+    assert sch.info()["n_blocks"] == -(-w.n // B)
+    y3 = sch.execute(Lv, Mv, b=b)
+    sch.reblock(0, 0, 1, 0)
+    y1 = sch.execute(Lv, Mv, b=b)
+    sch.check()
+    assert col_rel_err(host(y3), host(y)) < TOL[dtype] and col_rel_err(host(y1), host(y)) < TOL[dtype]
+
+
+def test_per_instance_block_order_matches_definition():
+    need_cuda()
+    w = I.batched_trsv_spmv(count=9, nmin=50, nmax=3000, seed=7)
+    Lb = _blockdiag([x.L for x in w.instances])
+    Mb = _blockdiag([x.M for x in w.instances])
+    sch = sf.inspect_batched("trsv_spmv", [dev_csr(x.L) for x in w.instances], [dev_csr(x.M) for x in w.instances])
+    sch.reblock(0, 0, 5, 0)
+    got = sch.export_blocks(0)
+    n = w.n
+    lev = oracle.levels(oracle.SEP, Lb, Mb)
+    inst = np.repeat(np.arange(len(w.instances)), [x.n for x in w.instances])
+    v = np.arange(2 * n)
+    key_inst = np.concatenate([inst, inst])
+    perm = np.lexsort((v, lev, key_inst))
+    ref = np.where(perm < n, perm, (perm - n) | (1 << 31)).astype(np.int64).astype(np.uint32).view(np.int32)
+    assert np.array_equal(got["order"], ref)
+    sizes = np.array([2 * x.n for x in w.instances])
+    assert np.array_equal(got["block_ptr"], np.concatenate([[0], np.cumsum(sizes)]))
+    ref_sp, ref_bs = oracle.block_segments(oracle.SEP, n, got["order"], got["block_ptr"], lev)
+    assert np.array_equal(got["seg_ptr"], ref_sp) and np.array_equal(got["block_seg"], ref_bs)
+    assert oracle.validate(oracle.SEP, Lb, Mb, got["order"], got["block_ptr"]) == 0

@@ -130,9 +130,10 @@ __device__ void cta_block(const ExecArgs &a, int mode, int r0, int r1, int p0, i
                 if constexpr (LV >= 3) {
                     const int li = row - r0;
                     const int rs = srp[li], dg = srp[li + 1] - 1;
-                    T acc = T(0);
-                    for (int e = rs; e < dg; ++e) acc += slv[e] * sx[slc[e]];
-                    sx[li] = (sx[li] - acc) * slv[dg];
+                    // b_i - L_i1 x_1 - L_i2 x_2 - ...: one dependent FP64 operation per entry
+                    T t = sx[li];
+                    for (int e = rs; e < dg; ++e) t = fma(-slv[e], sx[slc[e]], t);
+                    sx[li] = t * slv[dg];
                 } else {
                     const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
                     T acc = T(0);

@@ -382,30 +382,71 @@ __device__ bool grid_barrier(KahnCtl *ctl, unsigned nblocks, unsigned long long 
     return __syncthreads_and(ok) != 0;
 }
 
-// Decrements the in-degree of successor t (for 0 <= t) and appends it to the next frontier
-// when it reaches zero; the appends of a warp share one atomic on the frontier counter.
-__device__ __forceinline__ void kahn_visit(int t, int *__restrict__ indeg, int *__restrict__ queue, long long fe,
+constexpr int kKahnBatch = 8;      // successors per thread whose in-degree atomics are in flight together
+constexpr int kKahnThreads = 256;
+constexpr int kKahnLongDeg = 32 * kKahnBatch;   // longer successor lists are expanded by the whole block
+constexpr int kKahnMaxLong = 64;   // long vertices a block collects per round (more: expanded by their warp)
+
+// One batch of a frontier vertex's successors: entries k = k_first + stride * u (u <
+// kKahnBatch, k < deg) of the concatenated successor lists (first s1ci[a1 .. a1 + deg1), the
+// diagonal entry `self` skipped; then s2ci[a2 ..], offset by n1). Decrements each successor's
+// in-degree (all atomics in flight before any result is looked at) and appends those that
+// reach zero to the next frontier; the appends of a warp share one atomic on the frontier
+// counter. Every lane of the calling warp takes part.
+__device__ __forceinline__ void kahn_batch(int k_first, int stride, int deg1, int deg, const int *__restrict__ s1ci,
+                                           int a1, int self, const int *__restrict__ s2ci, int a2, int n1,
+                                           int *__restrict__ indeg, int *__restrict__ queue, long long fe,
                                            unsigned *cnt) {
-    const bool ready = t >= 0 && atomicSub(&indeg[t], 1) == 1;
-    const unsigned m = __ballot_sync(0xffffffffu, ready);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    const int lane = threadIdx.x & 31;
+    int t[kKahnBatch];
+#pragma unroll
+    for (int u = 0; u < kKahnBatch; ++u) {
+        const int k = k_first + stride * u;
+        t[u] = -1;
+        if (k < deg1) {
+            const int c = s1ci[a1 + k];
+            if (c != self) t[u] = c;
+        } else if (k < deg) {
+            t[u] = n1 + s2ci[a2 + k - deg1];
+        }
+    }
+    bool rd[kKahnBatch];
+#pragma unroll
+    for (int u = 0; u < kKahnBatch; ++u) rd[u] = t[u] >= 0 && atomicSub(&indeg[t[u]], 1) == 1;
+    int mine = 0;
+#pragma unroll
+    for (int u = 0; u < kKahnBatch; ++u) mine += rd[u] ? 1 : 0;
+    // inclusive prefix sum of `mine` over the warp, one append per batch
+    int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
     unsigned base = 0;
-    if (lane == leader) base = atomicAdd(cnt, (unsigned)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (ready) queue[fe + base + __popc(m & lanemask_lt())] = t;
+    if (lane == 31) base = atomicAdd(cnt, (unsigned)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    long long pos = fe + base + (incl - mine);
+#pragma unroll
+    for (int u = 0; u < kKahnBatch; ++u)
+        if (rd[u]) queue[pos++] = t[u];
 }
 
 // Frontier peeling: round r owns the vertices whose last predecessor was removed in
 // round r-1 (its level is r); removing a vertex decrements its successors' in-degrees and
-// appends those that reach zero to the next frontier. One warp expands one frontier vertex
-// (its lanes split the successor list, so long rows do not serialise on one thread).
-// Counters of the next frontier are triple-buffered so that no block reads a count while
-// another resets it.
-__global__ void __launch_bounds__(256) k_kahn(int n1, const int *__restrict__ s1rp, const int *__restrict__ s1ci,
-                                              const int *__restrict__ s2rp, const int *__restrict__ s2ci,
-                                              int *__restrict__ indeg, int *__restrict__ queue,
-                                              int *__restrict__ level, KahnCtl *ctl, unsigned long long tmo) {
+// appends those that reach zero to the next frontier. One warp expands one frontier vertex,
+// its lanes splitting the successor list; a vertex with more than kKahnLongDeg successors is
+// set aside and expanded by all the threads of the block once the block's warps are done, so
+// one long row costs a few atomic round trips instead of one per 256 successors. Counters of
+// the next frontier are triple-buffered so that no block reads a count while another resets it.
+__global__ void __launch_bounds__(kKahnThreads) k_kahn(int n1, const int *__restrict__ s1rp, const int *__restrict__ s1ci,
+                                                       const int *__restrict__ s2rp, const int *__restrict__ s2ci,
+                                                       int *__restrict__ indeg, int *__restrict__ queue,
+                                                       int *__restrict__ level, KahnCtl *ctl, unsigned long long tmo) {
+    __shared__ int s_long[kKahnMaxLong];
+    __shared__ int s_nlong;
     const unsigned nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,31 +454,40 @@ __global__ void __launch_bounds__(256) k_kahn(int n1, const int *__restrict__ s1
     const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
     long long fs = 0, fe = (long long)ld_acquire_u32(&ctl->nsrc);
     int round = 0;
+    if (threadIdx.x == 0) s_nlong = 0;
+    __syncthreads();
     while (fs < fe) {
         unsigned *cnt = &ctl->cnt[round % 3];
         for (long long idx = fs + gwarp; idx < fe; idx += nwarp) {
             const int v = queue[idx];
             if (lane == 0) level[v] = round;
-            if (v < n1) {
-                const int a1 = s1rp[v], b1 = s1rp[v + 1];
-                for (int e0 = a1; e0 < b1; e0 += 32) {
-                    const int e = e0 + lane;
-                    int t = -1;
-                    if (e < b1) {
-                        t = s1ci[e];
-                        if (t == v) t = -1;
-                    }
-                    kahn_visit(t, indeg, queue, fe, cnt);
-                }
-                if (s2rp) {
-                    const int a2 = s2rp[v], b2 = s2rp[v + 1];
-                    for (int e0 = a2; e0 < b2; e0 += 32) {
-                        const int e = e0 + lane;
-                        kahn_visit(e < b2 ? n1 + s2ci[e] : -1, indeg, queue, fe, cnt);
-                    }
+            if (v >= n1) continue;
+            const int a1 = s1rp[v], deg1 = s1rp[v + 1] - a1;
+            const int a2 = s2rp ? s2rp[v] : 0, deg = deg1 + (s2rp ? s2rp[v + 1] - a2 : 0);
+            if (deg > kKahnLongDeg) {
+                int slot = 0;
+                if (lane == 0) slot = atomicAdd(&s_nlong, 1);
+                slot = __shfl_sync(0xffffffffu, slot, 0);
+                if (slot < kKahnMaxLong) {
+                    if (lane == 0) s_long[slot] = v;
+                    continue;
                 }
             }
+            for (int k0 = 0; k0 < deg; k0 += 32 * kKahnBatch)
+                kahn_batch(k0 + lane, 32, deg1, deg, s1ci, a1, v, s2ci, a2, n1, indeg, queue, fe, cnt);
         }
+        __syncthreads();
+        const int nl = min(s_nlong, kKahnMaxLong);
+        for (int i = 0; i < nl; ++i) {
+            const int v = s_long[i];
+            const int a1 = s1rp[v], deg1 = s1rp[v + 1] - a1;
+            const int a2 = s2rp ? s2rp[v] : 0, deg = deg1 + (s2rp ? s2rp[v + 1] - a2 : 0);
+            for (int k0 = 0; k0 < deg; k0 += kKahnThreads * kKahnBatch)
+                kahn_batch(k0 + (int)threadIdx.x, kKahnThreads, deg1, deg, s1ci, a1, v, s2ci, a2, n1, indeg, queue, fe,
+                           cnt);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nlong = 0;
         if (gtid == 0) ctl->cnt[(round + 1) % 3] = 0u;
         if (!grid_barrier(ctl, nblocks, tmo)) return;
         const long long nf = (long long)ld_acquire_u32(cnt);
@@ -764,7 +814,7 @@ __global__ void k_block_keys(int kind, int n, long long nv, int B, int nb, int d
                              const int *__restrict__ Mrp, const int *__restrict__ Mci,
                              const int *__restrict__ MTrp, const int *__restrict__ MTci,
                              const int *__restrict__ inst_ptr, unsigned *__restrict__ keys,
-                             unsigned *__restrict__ vals, int *__restrict__ bcount) {
+                             unsigned *__restrict__ vals) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
         const bool rev = kind == K_PAIRED_T || kind == K_SEP_T;
         long long b;
@@ -784,7 +834,26 @@ __global__ void k_block_keys(int kind, int n, long long nv, int B, int nb, int d
         }
         keys[v] = (unsigned)(b * depth + level[v]);
         vals[v] = (unsigned)v;
-        atomicAdd(&bcount[b], 1);
+    }
+}
+
+// First position of every block in the sorted keys (block b's keys are b*depth .. b*depth +
+// depth - 1): a binary search per block, block_ptr[nb] = nv.
+__global__ void k_block_ptr(int nb, long long nv, unsigned depth, const unsigned *__restrict__ keys,
+                            int *__restrict__ block_ptr) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
+        if (b == nb) {
+            block_ptr[b] = (int)nv;
+            continue;
+        }
+        const unsigned key = (unsigned)b * depth;
+        long long lo = 0, hi = nv;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (keys[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        block_ptr[b] = (int)lo;
     }
 }
 
@@ -830,21 +899,18 @@ cudaError_t build_block_order(int kind, int n, long long nv, int B, int depth, c
     if ((unsigned long long)nb * (unsigned long long)std::max(depth, 1) > 0xffffffffull) return cudaErrorInvalidValue;
     unsigned *keys = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
     unsigned *vals = (unsigned *)ar.alloc(sizeof(unsigned) * nv);
-    int *cnt = (int *)ar.alloc(sizeof(int) * ((size_t)nb + 1));
     int *flag = (int *)ar.alloc(sizeof(int) * (size_t)nv);
     int *segidx = (int *)ar.alloc(sizeof(int) * ((size_t)nv + 1));
     int *out2 = (int *)ar.alloc(sizeof(int) * 2);
-    if (!keys || !vals || !cnt || !flag || !segidx || !out2) return cudaErrorMemoryAllocation;
-    cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)nb + 1), s);
+    if (!keys || !vals || !flag || !segidx || !out2) return cudaErrorMemoryAllocation;
     cudaMemsetAsync(out2, 0, sizeof(int) * 2, s);
     k_block_keys<<<grid_for(nv, 256, 4096), 256, 0, s>>>(kind, n, nv, B, nb, depth, level, M ? M->rowptr : nullptr,
                                                          M ? M->colidx : nullptr, MT ? MT->t.rowptr : nullptr,
-                                                         MT ? MT->t.colidx : nullptr, inst_ptr, keys, vals, cnt);
+                                                         MT ? MT->t.colidx : nullptr, inst_ptr, keys, vals);
     cudaError_t e = radix_sort_pairs(keys, vals, nv, bits_for((unsigned long long)nb * depth - 1), s, ar);
     if (e != cudaSuccess) return e;
     k_encode_order<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, n, vals, order);
-    e = scan_excl<int>(cnt, block_ptr, nb, s, ar);
-    if (e != cudaSuccess) return e;
+    k_block_ptr<<<grid_for((long long)nb + 1, 256, 4096), 256, 0, s>>>(nb, nv, (unsigned)depth, keys, block_ptr);
     k_seg_flags<<<grid_for(nv, 256, 4096), 256, 0, s>>>(nv, keys, flag);
     e = scan_excl<int>(flag, segidx, nv, s, ar);
     if (e != cudaSuccess) return e;

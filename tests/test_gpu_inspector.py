@@ -148,3 +148,40 @@ def test_g2_placement_matches_oracle(g2):
                 assert np.array_equal(got["order"], ref["order"])
                 assert np.array_equal(got["part_ptr"], ref["part_ptr"])
                 assert info["g2_placement" if which == 0 else "adj_g2_placement"] == (g2 if sep else 0)
+
+
+def _hub_lower(n, hubs, seed):
+    """Lower-triangular pattern whose first `hubs` rows are sources and every later row reads
+    all of them (plus its predecessor row): the hubs' successor lists hold n - hubs entries, the
+    later rows' own lists hubs + 1, long lists in both the forward and the reversed DAG."""
+    rows = []
+    for i in range(n):
+        if i < hubs:
+            cols = [i]
+        else:
+            cols = list(range(hubs)) + ([i - 1] if i - 1 >= hubs else []) + [i]
+        rows.append(cols)
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    ci = np.concatenate([np.asarray(r, np.int32) for r in rows])
+    vals = I.uniform_pm1(seed, I.S_VALUES, np.arange(len(ci), dtype=np.int64)) + (ci == np.repeat(np.arange(n), np.diff(rp))) * 4
+    return I.Csr(n, n, rp, ci, vals)
+
+
+@pytest.mark.parametrize("hubs", [3, 300, 700])
+def test_levels_with_long_successor_lists(hubs):
+    # successor lists far beyond what one warp expands in a batch: the hubs in the forward DAG,
+    # the later rows in the reversed one, hundreds of them in one round
+    need_cuda()
+    n = 6000
+    L = _hub_lower(n, hubs, 91)
+    M = I.band_random(n, 6, 400, 92)
+    sch = sf.inspect("trsv_spmv", dev_csr(L), dev_csr(M), want_adjoint=True)
+    info = sch.info()
+    for which, (kind, what) in enumerate([KIND_OF["trsv_spmv"], ADJ_OF["trsv_spmv"]]):
+        C = info["part_cost_target"] if which == 0 else info["adj_part_cost_target"]
+        W = info["wide_cost"] if which == 0 else info["adj_wide_cost"]
+        ref = oracle.schedule(kind, what, L, M, C, wide=W)
+        got = sch.export(which)
+        assert np.array_equal(got["level"], ref["level"])
+        assert got["depth"] == ref["depth"]
+        assert np.array_equal(got["order"], ref["order"])

@@ -457,7 +457,7 @@ sf_status build_dir(sf_schedule *S, Dir &d, int kind, int what, long long C_user
 }
 
 sf_status build_schedule(sf_schedule *S, const sf_options &o, cudaStream_t s) {
-    Arena tmp;
+    Arena tmp(s);
     unsigned long long pst = 0;
     SF_CK(check_pattern(S->L, 1, &pst, s, tmp), "pattern check");
     if (pst != ~0ull)
@@ -916,7 +916,7 @@ SF_API sf_status sf_inspect_batched(sf_pair pair, int32_t count, const sf_csr *L
     S->inst_rows.resize((size_t)count + 1);
     for (int t = 0; t < count; ++t) S->inst_rows[(size_t)t] = dl[(size_t)t].row_off;
     S->inst_rows[(size_t)count] = (int)n;
-    Arena tmp;
+    Arena tmp(s);
     auto alloc_csr = [&](DevCsr &d, long long nnz) {
         d.n_rows = d.n_cols = (int)n;
         d.nnz = nnz;
@@ -1284,7 +1284,7 @@ SF_API sf_status sf_schedule_recut(sf_schedule *S, int32_t which, int64_t part_c
         return fail(SF_ERR_INVALID_ARG, "team_lanes must be 0, 8 or 32");
     cudaStream_t s = (cudaStream_t)stream;
     SF_CK(cudaStreamSynchronize(s), "recut");      // no launch of this schedule may be in flight
-    Arena tmp;
+    Arena tmp(s);
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;
@@ -1304,7 +1304,7 @@ SF_API sf_status sf_schedule_replace(sf_schedule *S, int32_t which, int32_t g2_p
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
     cudaStream_t s = (cudaStream_t)stream;
     SF_CK(cudaStreamSynchronize(s), "replace");
-    Arena tmp;
+    Arena tmp(s);
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         Dir &d = *dirs[w];
@@ -1338,7 +1338,7 @@ SF_API sf_status sf_schedule_reblock(sf_schedule *S, int32_t which, int32_t bloc
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
     cudaStream_t s = (cudaStream_t)stream;
     SF_CK(cudaStreamSynchronize(s), "reblock");
-    Arena tmp;
+    Arena tmp(s);
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;
@@ -1449,7 +1449,7 @@ SF_API sf_status sf_schedule_set_slices(sf_schedule *S, int32_t which, int64_t c
     if (which == 1 && !S->adj.present) return fail(SF_ERR_UNSUPPORTED, "no adjoint schedule");
     cudaStream_t s = (cudaStream_t)stream;
     SF_CK(cudaStreamSynchronize(s), "slices");
-    Arena tmp;
+    Arena tmp(s);
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w) {
         if ((which != -1 && which != w) || !dirs[w]->present) continue;

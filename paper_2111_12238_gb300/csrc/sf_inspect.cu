@@ -6,6 +6,7 @@
 // (8-bit digits, per-block histograms, in-tile ranking with warp match), a count/scan/
 // sort transpose and a cooperative persistent Kahn kernel with a bounded grid barrier.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "sf_inspect.cuh"
@@ -13,10 +14,40 @@
 namespace sf {
 
 // ------------------------------------------------------------------------------ arena
+namespace {
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices];
+
+// The library's memory pool of the current device (created on first use), or NULL.
+cudaMemPool_t library_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = 1ull << 30;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = p;
+    }
+    return g_pool[dev];
+}
+}  // namespace
+
 void *Arena::alloc(size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaMemPool_t pool = pooled ? library_pool() : nullptr;
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, stream) : cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         oom = true;
         return nullptr;
@@ -25,7 +56,11 @@ void *Arena::alloc(size_t bytes) {
     return p;
 }
 Arena::~Arena() {
-    for (void *p : ptrs) cudaFree(p);
+    // pooled memory is returned in stream order, after the work that used it
+    for (void *p : ptrs) {
+        if (pooled && library_pool()) cudaFreeAsync(p, stream);
+        else cudaFree(p);
+    }
 }
 
 static inline unsigned grid_for(long long n, int threads, long long cap = 1 << 20) {

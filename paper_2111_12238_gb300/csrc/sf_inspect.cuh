@@ -9,9 +9,19 @@ namespace sf {
 
 // Device allocations that are released together (temporaries of one inspector call, or
 // the arrays a schedule owns).
+// Device allocations released together. A temporary arena (constructed with a stream) takes
+// stream-ordered memory from the library's pool of the current device, which keeps up to
+// 1 GiB of freed memory for the next inspection instead of returning it to the driver; a
+// persistent arena (no stream) uses cudaMalloc.
 struct Arena {
     std::vector<void *> ptrs;
     bool oom = false;
+    bool pooled = false;
+    cudaStream_t stream = nullptr;
+    Arena() = default;
+    explicit Arena(cudaStream_t s) : pooled(true), stream(s) {}
+    Arena(const Arena &) = delete;
+    Arena &operator=(const Arena &) = delete;
     void *alloc(size_t bytes);
     ~Arena();
 };

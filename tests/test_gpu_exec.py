@@ -332,6 +332,8 @@ def test_recut_and_autotune_keep_results_exact():
         elif r["exec"] in ("ws", "tma"):
             assert inf[pre + "exec_mode"] == (3 if r["exec"] == "ws" else 4)
             assert inf[pre + "block_rows"] == r["block_rows"]
+        elif r["exec"] == "cta":
+            assert pre == "" and inf["exec_mode"] == 5 and inf["n_blocks"] == 1
         else:
             assert inf[pre + "exec_mode"] == 1 and r["lanes"] in autotune.DEFAULT_LANES
             assert inf[pre + "lanes_per_row"] == r["lanes"]

@@ -87,6 +87,7 @@ struct Dir {
     bool per_inst = false;      // blocks are the instances (single-CTA executor), not B rows
     int *bperm = nullptr;       // per-instance blocks: launch order, costliest block first
     int cta_per_sm = 0;         // single-CTA executor: CTAs per SM (0 automatic)
+    void *cta_vbuf = nullptr;   // single-CTA executor: x handed to the helper CTAs (n doubles, reset)
     void *aux = nullptr;        // (c_i, 1 / L_ii) per row, written by the row-block pre-pass
     // packed records of the row-block order (exec_mode 4), built when that mode is chosen
     void *pmeta = nullptr, *pvals = nullptr, *paux = nullptr;
@@ -693,8 +694,19 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
         a.block_seg = d.block_seg;
         a.block_ptr = d.block_ptr;
         a.n_blocks = d.nb;
-        const cudaError_t e = launch_cta_exec(mode, dtype, S->inst_ptr, d.bperm, d.cta_per_sm, S->sms, s, a,
-                                              d.ev_start, d.ev_stop);
+        // a single SpTRSV -> SpMV system hands x to helper CTAs through a flag buffer that every
+        // launch leaves reset (all bits set)
+        if (mode == M_TRSV_SPMV && d.nb == 1 && !d.cta_vbuf) {
+            sf_schedule *Sm = const_cast<sf_schedule *>(S);
+            std::lock_guard<std::mutex> lk(Sm->mu);
+            Dir &dm = const_cast<Dir &>(d);
+            dm.cta_vbuf = Sm->keep.alloc(sizeof(double) * (size_t)std::max(S->n, 1));
+            if (!dm.cta_vbuf) return fail(SF_ERR_OOM, "single-CTA executor: out of device memory");
+            SF_CK(cudaMemsetAsync(dm.cta_vbuf, 0xff, sizeof(double) * (size_t)std::max(S->n, 1), s), "single-CTA executor");
+        }
+        const cudaError_t e = launch_cta_exec(mode, dtype, S->inst_ptr, d.bperm, d.cta_per_sm, S->sms,
+                                              mode == M_TRSV_SPMV ? d.cta_vbuf : nullptr, s, a, d.ev_start,
+                                              d.ev_stop);
         if (e != cudaSuccess) return from_cuda(e, "single-CTA executor launch");
         return SF_OK;
     }

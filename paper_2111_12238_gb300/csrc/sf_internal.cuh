@@ -41,7 +41,8 @@ struct ExecState {
     unsigned abort;
     unsigned err_code;
     int err_row;
-    unsigned pad0, pad1;
+    unsigned pad0;
+    unsigned cta_exit;   // single-CTA executor with helper CTAs: CTAs of the launch that have finished
 };
 
 // Argument block of the executor. Typed pointers are carried as void* and cast in the
@@ -141,8 +142,10 @@ int occupancy_next(int mode, int dtype, int lpr, bool vf, int team, int minb);
 // Single-CTA executor (exec_mode 5, k = 1): one CTA per block of the per-instance row-block
 // order (a.order, a.seg_ptr, a.block_ptr, a.block_seg, a.n_blocks; inst_ptr the instances'
 // first rows; bperm the launch order of the blocks), cta_per_sm CTAs per SM (0 automatic).
+// vbuf: n values of 8 bytes with every bit set, through which a single SpTRSV -> SpMV system
+// hands x to its helper CTAs (left in that state by every launch); NULL runs no helpers.
 cudaError_t launch_cta_exec(int mode, int dtype, const int *inst_ptr, const int *bperm, int cta_per_sm, int sms,
-                            cudaStream_t s, const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop);
+                            void *vbuf, cudaStream_t s, const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop);
 constexpr int kIluMaxRow = 256;   // longest row of A an ILU0 row keeps on chip
 int occupancy_fwd(int mode, int dtype, int lpr, bool vf, int team, int minb);
 int occupancy_pair(int mode, int dtype, int lpr, bool vf, int team, int minb);

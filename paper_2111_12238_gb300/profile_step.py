@@ -2,6 +2,7 @@
 
     python -m paper_2111_12238_gb300.profile_step [n] [steps]
     python -m paper_2111_12238_gb300.profile_step lap2d [nx] [steps]
+    python -m paper_2111_12238_gb300.profile_step lap3d [nx] [steps]
 
 The first form runs the power-law SpMV -> SpTRSV workload: the fused forward with L read from
 A's rows, then the fused adjoint with both value gradients. n = 4,194,304 is the powerlaw4m
@@ -11,7 +12,12 @@ lanes per row, cost target 26, rows costlier than 64 split over teams; adjoint 1
 row, cost target 14, two-block kernels.
 
 The second form runs the SpTRSV -> SpMV pair on the nx x nx 5-point grid (nx = 64 is the
-lap2d64 workload, seed 1) on the single-CTA executor, the shape the autotuner picks there."""
+lap2d64 workload, seed 1) on the single-CTA executor, the shape the autotuner picks there.
+
+The third runs the SpTRSV -> SpMV pair on nx^3 (nx = 128 is the lap3d128 workload: lower
+7-point L, banded M, seed 2), forward and adjoint with both value gradients, in the shapes the
+autotuner picks there: forward on partitions (one lane per row, cost target 112, second-kernel
+rows 32 wavefronts late), adjoint on the warp-specialised row blocks of 16384 rows."""
 import os
 import sys
 
@@ -50,6 +56,21 @@ def _lap2d(nx, steps, sf, I, dev):
     return sch
 
 
+def _lap3d(nx, steps, sf, I, dev):
+    w = I.trsv_spmv_lap3d_band(nx)
+    sch = sf.inspect("trsv_spmv", sf.DeviceCsr.from_host(w.L), sf.DeviceCsr.from_host(w.M), want_adjoint=True,
+                     g2_placement=32)
+    sch.recut(0, 112, 1, 32)
+    sch.reblock(1, 16384, 3, 0)
+    Lv, Mv, b, gy = dev(w.L.vals), dev(w.M.vals), dev(w.b), dev(w.gy)
+    xs, y, gb = torch.empty_like(b), torch.empty_like(b), torch.empty_like(b)
+    gL, gM = torch.empty_like(Lv), torch.empty_like(Mv)
+    for _ in range(steps):
+        sch.execute(Lv, Mv, b=b, x_save=xs, y=y)
+        sch.adjoint(Lv, Mv, gy, saved=xs, gb=gb, gL=gL, gM=gM)
+    return sch
+
+
 def main():
     import __graft_entry__
     __graft_entry__.build()
@@ -57,10 +78,10 @@ def main():
     from paper_2111_12238_gb300 import sparsefusion as sf
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
     args = sys.argv[1:]
-    if args and args[0] == "lap2d":
-        size = int(args[1]) if len(args) > 1 else 64
+    if args and args[0] in ("lap2d", "lap3d"):
+        size = int(args[1]) if len(args) > 1 else (64 if args[0] == "lap2d" else 128)
         steps = int(args[2]) if len(args) > 2 else 1
-        sch = _lap2d(size, steps, sf, I, dev)
+        sch = (_lap2d if args[0] == "lap2d" else _lap3d)(size, steps, sf, I, dev)
     else:
         size = int(args[0]) if args else (1 << 22)
         steps = int(args[1]) if len(args) > 1 else 1

@@ -462,6 +462,7 @@ def measure(wl, args, device, world, rank, hw):
             g.unfused_adj()
     g.check()
     tuned = {}
+    packing_ablation = None
     if not args.no_tune:
         # the project's autotuner picks each pass's launch shape, the unfused paths included
         kw = dict(dtype=g.dt, k=wl["k"], budget_s=args.tune_seconds, use_cache=False)
@@ -472,6 +473,14 @@ def measure(wl, args, device, world, rank, hw):
             tuned["unfused"] = autotune.tune(g.un_sched, g.unfused, which=0, **kw)
         if adj:
             tuned["unfused_adj"] = autotune.tune(g.un_adj, g.unfused_adj, which=0, **kw)
+        # packing ablation (§3.2.3, Fig. 7): the forward's best interleaved and separated trials
+        if wl["pair"] == "spmv_trsv":
+            tr = tuned["fwd"]["trials"]
+            inter = [t["ms"] for t in tr if t.get("packing", 1) == 1]
+            sep = [t["ms"] for t in tr if t.get("packing", 1) == 0]
+            packing_ablation = {"interleaved_ms": min(inter) if inter else None,
+                                "separated_ms": min(sep) if sep else None,
+                                "how": "autotuner trials of the fused forward, same launch shape, median of 3"}
         for v in tuned.values():
             v.pop("trials", None)
     steps = args.steps
@@ -614,6 +623,7 @@ def measure(wl, args, device, world, rank, hw):
         "inspect_ms": g.inspect_s * 1e3,
         "ner_vs_unfused": (g.inspect_s * 1e3 / (un_ms - fwd_ms)) if (un_ms and un_ms > fwd_ms) else None,
         "tuned": tuned,
+        "packing_ablation": packing_ablation,
         "e2e": {"value": job_value(world, e2e_steps, e2e_s * 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         # our kernels per step, as the library counts them for the tuned launch shapes:

@@ -364,6 +364,18 @@ sf_status sf_schedule_set_slices(sf_schedule *sch, int32_t which, int64_t cost_p
  * above k, at most 32). Chosen per direction by the autotuner. No GPU work. */
 sf_status sf_schedule_set_rhs_tile(sf_schedule *sch, int32_t which, int32_t rhs_tile);
 
+/* Packing of the forward pass of an SF_SPMV_TRSV schedule (§3.2.3): 1 interleaved (default;
+ * each paired row computes r_i = b_i - A_i x_in in registers, then its solve row), 0 separated
+ * (the SpMV vertices first: every group of the partition executor computes r_i for its share
+ * of the rows, in increasing row order, before it takes partitions, and publishes it by value
+ * in a buffer of n x k values the library owns; the solve rows, split over teams or not, then
+ * wait for their r_i and walk L's strict part only). Separated packing needs a value-flag
+ * launch (k = 1, or 16 or more lanes per row) of the partition executor on its one- or
+ * two-block kernels (sf_schedule_set_occupancy 1 or 2); other launches return
+ * SF_ERR_UNSUPPORTED. The levels and order are the same for both. Other pairs:
+ * SF_ERR_UNSUPPORTED. sf_schedule_info reports the choice in `packing`. No GPU work. */
+sf_status sf_schedule_set_packing(sf_schedule *sch, int32_t packing);
+
 /* Copies a row-block schedule to HOST buffers: order[n_items] (row | kernel << 31, sorted
  * by (block, level, kernel, row)), block_ptr[n_blocks+1], seg_ptr[block_segments+1] (first
  * position of every level segment: a maximal run of positions with the same block and

@@ -94,6 +94,8 @@ def _apply(sched: sf.Schedule, which: int, c: Dict, mean: int):
     sched.set_occupancy(which, c.get("occ", 1))
     sched.set_rhs_tile(which, c.get("rt", 0))
     sched.set_slices(which, c.get("slices", 0) if c["exec"] == "partitions" else 0)
+    if sched.pair == "spmv_trsv" and which == 0:
+        sched.set_packing(c.get("packing", 1))
     if c["exec"] == "cta":
         sched.reblock(which, 0, 5, c.get("cps", 0))
         sched.set_split(which, 0)
@@ -116,7 +118,7 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
          block_rows: Sequence[int] = DEFAULT_BLOCK_ROWS, block_lanes: Sequence[int] = DEFAULT_BLOCK_LANES,
          splits: Sequence[int] = DEFAULT_SPLITS, placements: Sequence[int] = DEFAULT_PLACEMENTS, occupancy=True,
          rhs_tiles: Sequence[int] = DEFAULT_RHS_TILES, slices: Sequence[int] = DEFAULT_SLICES,
-         reps: int = 3, budget_s: float = 20.0,
+         packing: bool = True, reps: int = 3, budget_s: float = 20.0,
          use_cache: bool = True) -> Dict:
     """Chooses the executor and its launch shape for `which` (0 forward, 1 adjoint) of
     `sched`, timing `run()` (one execution) for every candidate within `budget_s` seconds.
@@ -257,6 +259,22 @@ def tune(sched: sf.Schedule, run: Callable[[], object], *, which: int = 0, dtype
             trials.append(dict(c, ms=ms))
             if ms < best["ms"]:
                 best = trials[-1]
+    # SpMV -> SpTRSV: separated packing (r = b - A x_in first, §3.2.3) on the best partition shape
+    if best is not None and best["exec"] == "partitions" and sched.pair == "spmv_trsv" and which == 0 and packing:
+        c = {kk: v for kk, v in best.items()
+             if kk in ("exec", "lanes", "items", "team", "g2", "occ", "rt", "slices")}
+        c["packing"] = 0
+        if c.get("occ") == 3:
+            c.pop("occ")   # the three-block kernels do not run separated packing
+        try:
+            _apply(sched, which, c, mean)
+            ms = _time(run, reps)
+            sched.check()
+            trials.append(dict(c, ms=ms))
+            if ms < best["ms"]:
+                best = trials[-1]
+        except sf.SparseFusionError:
+            pass   # a launch that does not publish through values
     if best is not None and best["exec"] == "partitions" and splits and separated:
         for pct in splits:
             c = {kk: v for kk, v in best.items()

@@ -88,6 +88,8 @@ struct Dir {
     int *bperm = nullptr;       // per-instance blocks: launch order, costliest block first
     int cta_per_sm = 0;         // single-CTA executor: CTAs per SM (0 automatic)
     void *cta_vbuf = nullptr;   // single-CTA executor: x handed to the helper CTAs (n doubles, reset)
+    void *rsep = nullptr;       // SpMV -> SpTRSV with separated packing: r (value flags), rsep_bytes
+    size_t rsep_bytes = 0;
     void *aux = nullptr;        // (c_i, 1 / L_ii) per row, written by the row-block pre-pass
     // packed records of the row-block order (exec_mode 4), built when that mode is chosen
     void *pmeta = nullptr, *pvals = nullptr, *paux = nullptr;
@@ -682,8 +684,27 @@ sf_status launch(const sf_schedule *S, const Dir &d, int mode, sf_dtype dt, int 
     const bool shared = mode == M_SPMV_TRSV && a.Lv == nullptr;
     if (shared && !vf)
         return fail(SF_ERR_UNSUPPORTED, "L read from A's rows needs value flags: k = 1, or at least 16 lanes per row");
+    // separated packing of SpMV -> SpTRSV (the forward): r = b - A x_in is computed by every group
+    // of the partition executor before it takes partitions, published by value (reset here)
+    const bool sep = mode == M_SPMV_TRSV && S->packing == 0;
+    a.rsep = nullptr;
+    if (sep) {
+        if (!vf) return fail(SF_ERR_UNSUPPORTED, "separated packing needs value flags: k = 1, or at least 16 lanes per row");
+        if (d.minb >= 3) return fail(SF_ERR_UNSUPPORTED, "separated packing runs on the one- and two-block kernels");
+        const size_t bytes = (size_t)S->n * (size_t)k * (dt == SF_F64 ? 8 : 4);
+        if (bytes > d.rsep_bytes) {
+            sf_schedule *Sm = const_cast<sf_schedule *>(S);
+            std::lock_guard<std::mutex> lk(Sm->mu);
+            Dir &dm = const_cast<Dir &>(d);
+            dm.rsep = Sm->keep.alloc(std::max<size_t>(bytes, 16));
+            if (!dm.rsep) return fail(SF_ERR_OOM, "separated packing: out of device memory");
+            dm.rsep_bytes = bytes;
+        }
+        SF_CK(cudaMemsetAsync(d.rsep, 0xff, bytes, s), "separated packing");
+        a.rsep = d.rsep;
+    }
     // the row-block executors serve one right-hand side
-    const bool rows1 = vf && !ic0 && k == 1 && !shared;
+    const bool rows1 = vf && !ic0 && k == 1 && !shared && !sep;
     // single-CTA executor: small systems whose whole row-block order is one block
     if (d.exec_mode == 5) {
         if ((mode != M_TRSV_SPMV && mode != M_TRSV) || k != 1 || a.Lv == nullptr)
@@ -1451,6 +1472,15 @@ SF_API sf_status sf_schedule_set_rhs_tile(sf_schedule *S, int32_t which, int32_t
     Dir *dirs[2] = {&S->fwd, &S->adj};
     for (int w = 0; w < 2; ++w)
         if ((which == -1 || which == w) && dirs[w]->present) dirs[w]->kt = rhs_tile;
+    return SF_OK;
+}
+
+SF_API sf_status sf_schedule_set_packing(sf_schedule *S, int32_t packing) {
+    if (!S) return fail(SF_ERR_INVALID_ARG, "schedule is NULL");
+    if (packing != 0 && packing != 1) return fail(SF_ERR_INVALID_ARG, "packing must be 0 (separated) or 1 (interleaved)");
+    if (S->pair != SF_SPMV_TRSV)
+        return fail(SF_ERR_UNSUPPORTED, "the packing of the forward pass can be chosen for SF_SPMV_TRSV only");
+    S->packing = packing;
     return SF_OK;
 }
 

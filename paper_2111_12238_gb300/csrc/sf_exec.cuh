@@ -613,13 +613,58 @@ __device__ bool item_spmv_dep(const ExecArgs &a, int row, unsigned epoch, int gl
     return group_ok<LPR>(ok, gmask);
 }
 
+// Solve row of a separated SpMV -> SpTRSV (§3.2.3): r_i was computed before the partitions by
+// some group of the launch; only the solve row remains, over L's strict part (A's entries
+// before the diagonal in shared storage). Kept out of line so that the paired item's register
+// budget does not grow.
+template <typename T, int LPR, int VU>
+__device__ __noinline__ bool item_spmv_trsv_sep(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask,
+                                                int ra) {
+    const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
+    int lo, hi;
+    const int *cols;
+    const T *vals;
+    T d;
+    if (a.Lv == nullptr) {
+        const int dp = __ldg(a.a_diag + row);
+        lo = ra;
+        hi = dp;
+        cols = a.Mci;
+        vals = (const T *)a.Mv;
+        d = load_diag<T>(a, vals, dp, row, gl);
+    } else {
+        lo = __ldg(a.Lrp + row);
+        hi = __ldg(a.Lrp + row + 1) - 1;
+        cols = a.Lci;
+        vals = (const T *)a.Lv;
+        d = load_diag<T>(a, vals, hi, row, gl);
+    }
+    const T *r = (const T *)a.rsep;
+    T *z = (T *)a.y;
+    bool ok = true;
+    for (int c0 = 0; c0 < k; c0 += kt) {
+        const int c = c0 + cl;
+        const bool act = c < k;
+        T acc = row_dot<T, D_VALUE, false, VU>(cols, nullptr, vals, lo + s, hi, S, z, k, c, act, a.flags, epoch,
+                                               a.st, a.timeout_ns, row, ok);
+        acc = slice_sum<LPR>(acc, kt, gmask);
+        if (s == 0 && act) {
+            const T ri = poll_value(r + (size_t)row * k + c, a.st, a.timeout_ns, row, ok);
+            put_value(z + (size_t)row * k + c, finish_row<T>(a, ri - acc, d));
+        }
+    }
+    return group_ok<LPR>(ok, gmask);
+}
+
 // Paired SpMV -> SpTRSV row (combination 2, F = I): r_i = b_i - A_i x_in stays in
 // registers, then z_i = (r_i - sum_{j<i} L_ij z_j) / L_ii.
-template <typename T, int LPR, bool VF, int VU = value_unroll(LPR)>
+template <typename T, int LPR, bool VF, int VU = value_unroll(LPR), bool SEP = true>
 __device__ bool item_spmv_trsv(const ExecArgs &a, int row, unsigned epoch, int gl, unsigned gmask) {
     const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
     const int ra = __ldg(a.Mrp + row), re = __ldg(a.Mrp + row + 1);
     if constexpr (VF) {
+        if constexpr (SEP)
+            if (a.rsep) return item_spmv_trsv_sep<T, LPR, VU>(a, row, epoch, gl, gmask, ra);
         if (a.Lv == nullptr) {
             // shared storage (Table 2 combination 2 as one Gauss-Seidel half-sweep): L = tril(A) is
             // read from A's row, which is streamed once for both r_i and the solve
@@ -1039,6 +1084,73 @@ __device__ __forceinline__ void slice_range(int e0, int e1, int s, int m, int &l
     hi = s == m - 1 ? e1 : min(e1, lo + chunk);
 }
 
+// One slice of a separated SpMV -> SpTRSV solve row (r_i computed before the partitions): as
+// run_slice, with the slices splitting L's strict part (A's entries before the diagonal in
+// shared storage) and the owner's right-hand side r_i waited for by value. Out of line so that
+// the other kinds' slices keep their register budget.
+template <typename T, int LPR, int VU>
+__device__ __noinline__ bool run_slice_sep(const ExecArgs &a, int row, int s, int m, int slot, int gl,
+                                           unsigned gmask) {
+    const int kt = a.kt, S = LPR / kt, ls = gl / kt, cl = gl % kt, k = a.k;
+    const bool owner = s == m - 1;
+    T *parts = (T *)a.parts;
+    T *z = (T *)a.y;
+    const T *r = (const T *)a.rsep;
+    bool ok = true;
+    int lo, hi;
+    const int *cols;
+    const T *vals;
+    T d = T(0);
+    if (a.Lv == nullptr) {
+        const int ra = __ldg(a.Mrp + row), dp = __ldg(a.a_diag + row);
+        slice_range(ra, dp, s, m, lo, hi);
+        cols = a.Mci;
+        vals = (const T *)a.Mv;
+        if (owner) d = load_diag<T>(a, vals, dp, row, gl);
+    } else {
+        const int rs = __ldg(a.Lrp + row), dg = __ldg(a.Lrp + row + 1) - 1;
+        slice_range(rs, dg, s, m, lo, hi);
+        cols = a.Lci;
+        vals = (const T *)a.Lv;
+        if (owner) d = load_diag<T>(a, vals, dg, row, gl);
+    }
+    for (int c0 = 0; c0 < k; c0 += kt) {
+        const int c = c0 + cl;
+        const bool act = c < k;
+        T aw = row_dot<T, D_VALUE, false, VU>(cols, nullptr, vals, lo + ls, hi, S, z, k, c, act, nullptr, 0u, a.st,
+                                               a.timeout_ns, row, ok);
+        const T p = slice_sum<LPR>(aw, kt, gmask);
+        if (!owner) {
+            if (ls == 0 && act) put_value(parts + (size_t)(slot + s) * k + c, p);
+            continue;
+        }
+        T help = T(0);
+        if (m > 1) {
+            T hs = T(0);
+            if (act)
+                for (int h0 = ls; h0 < m - 1 && ok; h0 += 4 * S) {
+                    int j[4];
+                    T xv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int h = h0 + u * S;
+                        j[u] = h < m - 1 ? (slot + h) * k + c : -1;
+                    }
+                    ok = wait_values<T, 4>(parts, j, xv, a.st, a.timeout_ns, row);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (j[u] >= 0) hs += xv[u];
+                }
+            help = slice_sum<LPR>(hs, kt, gmask);
+        }
+        if (ls == 0 && act) {
+            const T ri = poll_value(r + (size_t)row * k + c, a.st, a.timeout_ns, row, ok);
+            put_value(z + (size_t)row * k + c, finish_row<T>(a, ri - (help + p), d));
+        }
+    }
+    return group_ok<LPR>(ok, gmask);
+}
+
 // One slice of a long row split at execution time (whole team, value flags). The row's dot
 // products are cut into m chunks of entries; slices 0 .. m-2 (the helpers, earlier in the
 // queue) each add up their chunk and store the partial sums (one per right-hand-side column)
@@ -1049,8 +1161,10 @@ __device__ __forceinline__ void slice_range(int e0, int e1, int s, int m, int &l
 // teams thus stream one long row as its inputs arrive. Kinds: SpTRSV rows (SpTRSV -> SpMV
 // tag 0, SpTRSV alone), SpMV -> SpTRSV rows (A and L parts, or A's row in shared storage) and
 // the transposed solve rows of the adjoints.
-template <int MODE, typename T, int LPR, int VU>
+template <int MODE, typename T, int LPR, int VU, bool SEP = true>
 __device__ bool run_slice(const ExecArgs &a, int tag, int row, int s, int m, int slot, int gl, unsigned gmask) {
+    if constexpr (MODE == M_SPMV_TRSV && SEP)
+        if (a.rsep) return run_slice_sep<T, LPR, VU>(a, row, s, m, slot, gl, gmask);
     const int kt = a.kt, S = LPR / kt, ls = gl / kt, cl = gl % kt, k = a.k;
     const bool owner = s == m - 1;
     T *parts = (T *)a.parts;
@@ -1178,7 +1292,9 @@ constexpr bool mode_has_vf(int m) {
            m == M_IC0_TRSV || m == M_IC0 || m == M_TRSV_TRSV || m == M_ILU0_TRSV;
 }
 
-template <int MODE, typename T, int LPR, bool VF, int VU>
+// SEP: the kernel carries the separated SpMV -> SpTRSV rows (not the three-block kernels,
+// whose register budget has no room for them).
+template <int MODE, typename T, int LPR, bool VF, int VU, bool SEP = true>
 __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, unsigned epoch, int gl, int gbase,
                                          unsigned gmask) {
     if constexpr (MODE == M_TRSV_SPMV) {
@@ -1187,7 +1303,7 @@ __device__ __forceinline__ bool run_item(const ExecArgs &a, int tag, int row, un
     } else if constexpr (MODE == M_TRSV) {
         return item_trsv<T, LPR, VF, VU>(a, row, epoch, gl, gmask, (T *)a.y);
     } else if constexpr (MODE == M_SPMV_TRSV) {
-        return item_spmv_trsv<T, LPR, VF, VU>(a, row, epoch, gl, gmask);
+        return item_spmv_trsv<T, LPR, VF, VU, SEP>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0_TRSV) {
         return item_ic0<T, LPR, true, VF>(a, row, epoch, gl, gmask);
     } else if constexpr (MODE == M_IC0) {
@@ -1240,6 +1356,28 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
     const int nteams = gridDim.x * (blockDim.x >> 5) * NT;
     const int team = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * NT + lane / TEAM;
     bool ok = true;
+    if constexpr (VF && MODE == M_SPMV_TRSV && MINB < 3) {
+        if (a.rsep) {
+            // separated packing (§3.2.3, the SpMV vertices in the first wavefront): every group
+            // computes r_i = b_i - A_i x_in for its share of the rows, in increasing row order,
+            // and publishes it by value; nothing here waits
+            const int kt = a.kt, S = LPR / kt, s = gl / kt, cl = gl % kt, k = a.k;
+            const T *Av = (const T *)a.Mv, *b = (const T *)a.b;
+            T *r = (T *)a.rsep;
+            const int ngroups = nteams * G;
+            for (int i = team * G + grp; i < a.n; i += ngroups) {
+                const int ra = __ldg(a.Mrp + i), re = __ldg(a.Mrp + i + 1);
+                for (int c0 = 0; c0 < k; c0 += kt) {
+                    const int c = c0 + cl;
+                    const bool act = c < k;
+                    T ax = row_dot<T, D_NONE, false>(a.Mci, nullptr, Av, ra + s, re, S, (const T *)a.xin, k, c, act,
+                                                     nullptr, 0u, a.st, a.timeout_ns, i, ok);
+                    ax = slice_sum<LPR>(ax, kt, gmask);
+                    if (s == 0 && act) put_value(r + (size_t)i * k + c, __ldg(b + (size_t)i * k + c) - ax);
+                }
+            }
+        }
+    }
     // A team holds its current partition (and with tickets the ticket of its next one);
     // every team runs its partitions in increasing order (within its class), so the smallest
     // unfinished partition is always being run by a team whose dependences are all finished.
@@ -1278,7 +1416,7 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
                 // one slice of a long row split over several teams
                 const unsigned o = (unsigned)__ldg(a.order + q0);
                 if (ok)
-                    ok = run_slice<MODE, T, TEAM, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), sl.y,
+                    ok = run_slice<MODE, T, TEAM, value_unroll(LPR), (MINB < 3)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), sl.y,
                                                                      sl.z, sl.w, tl, tmask);
                 if (!__all_sync(tmask, ok)) break;
                 if (a.dynamic) u = __shfl_sync(tmask, un_first, tbase);
@@ -1293,12 +1431,12 @@ __global__ void __launch_bounds__(kExecThreads, MINB) k_exec(const ExecArgs a) {
             // a long row: the whole team runs it (the cut gives it a partition of its own)
             const unsigned o = (unsigned)__ldg(a.order + q0);
             if (ok)
-                ok = run_item<MODE, T, TEAM, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl,
+                ok = run_item<MODE, T, TEAM, VF, value_unroll(LPR), (MINB < 3)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, tl,
                                                                     tbase, tmask);
         } else {
             for (int q = q0 + grp; q < q1 && ok; q += G) {
                 const unsigned o = (unsigned)__ldg(a.order + q);
-                ok = run_item<MODE, T, LPR, VF, value_unroll(LPR)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl,
+                ok = run_item<MODE, T, LPR, VF, value_unroll(LPR), (MINB < 3)>(a, (int)(o >> 31), (int)(o & 0x7fffffffu), epoch, gl,
                                                                    gbase, gmask);
             }
         }

@@ -98,6 +98,9 @@ struct ExecArgs {
     const int4 *xlist;
     int nx;
     void *parts;
+    // SpMV -> SpTRSV with separated packing (value flags): r = b - A x_in, n x k values, each its
+    // own flag; computed by every group of the launch before it takes partitions. NULL: paired.
+    void *rsep;
 };
 
 // launchers, one translation unit per group of modes (dtype: 0 f64, 1 f32)

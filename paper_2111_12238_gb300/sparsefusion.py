@@ -99,6 +99,7 @@ _SIGS = {
     "sf_schedule_set_split": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_set_slices": (C.c_int, [_P, C.c_int32, C.c_int64, _P]),
     "sf_schedule_set_rhs_tile": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "sf_schedule_set_packing": (C.c_int, [_P, C.c_int32]),
     "sf_schedule_replace": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "sf_schedule_set_occupancy": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "sf_schedule_set_ic0_pairs": (C.c_int, [_P, C.c_int32]),
@@ -360,6 +361,10 @@ class Schedule:
     def set_rhs_tile(self, which=-1, rhs_tile=0):
         """Right-hand-side columns a row's lanes handle side by side (0: automatic)."""
         _check(load_library().sf_schedule_set_rhs_tile(self.handle, which, int(rhs_tile)), "sf_schedule_set_rhs_tile")
+
+    def set_packing(self, packing: int):
+        """SpMV -> SpTRSV forward: 1 interleaved (paired rows), 0 separated (r first)."""
+        _check(load_library().sf_schedule_set_packing(self.handle, int(packing)), "sf_schedule_set_packing")
 
     def set_timeout(self, ns: int):
         _check(load_library().sf_schedule_set_timeout(self.handle, int(ns)), "sf_schedule_set_timeout")

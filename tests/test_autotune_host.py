@@ -53,6 +53,9 @@ class FakeSched:
     def set_slices(self, which, cost):
         self.state["slices"] = cost
 
+    def set_packing(self, packing):
+        self.state["packing"] = packing
+
     def check(self):
         pass
 
@@ -152,3 +155,14 @@ def test_batches_try_the_single_cta_executor_at_each_sm_share(fake_timing):
     fake_timing["sched"] = s1
     r1 = autotune.tune(s1, lambda: None, k=1, budget_s=60, use_cache=False)
     assert not any(t["exec"] == "cta" for t in r1["trials"])
+
+
+def test_spmv_trsv_tries_separated_packing(fake_timing):
+    # SpMV -> SpTRSV forward: the best partition shape is also timed with separated packing,
+    # and every other candidate runs interleaved
+    s = FakeSched(pair="spmv_trsv", separated=False)
+    fake_timing["sched"] = s
+    r = autotune.tune(s, lambda: None, k=1, budget_s=60, use_cache=False)
+    sep = [t for t in r["trials"] if t.get("packing") == 0]
+    assert len(sep) == 1 and sep[0]["exec"] == "partitions"
+    assert s.state["packing"] == r.get("packing", 1)

@@ -62,9 +62,13 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _csrc_hash():
+def _csrc_hash(files=None):
+    """Hash of the named sources under csrc/ (all of them when `files` is None)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2111_12238_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_2111_12238_gb300", "csrc")
+    paths = sorted(glob.glob(os.path.join(csrc, "*"))) if files is None else \
+        [os.path.join(csrc, f) for f in sorted(files)]
+    for f in paths:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
@@ -72,15 +76,20 @@ def _csrc_hash():
 
 
 def _recorded_traffic(workload, kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources; else None."""
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    sources of that kernel (the files the record lists, else every source); else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("csrc_hash") != _csrc_hash():
+    if not e:
+        return None
+    try:
+        if e.get("csrc_hash") != _csrc_hash(e.get("sources")):
+            return None
+    except OSError:
         return None
     return e.get("bytes_per_launch")
 

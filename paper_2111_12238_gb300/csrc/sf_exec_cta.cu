@@ -21,6 +21,7 @@
 // L2 while the block was staged.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "sf_exec.cuh"
 
@@ -216,8 +217,8 @@ __device__ __forceinline__ void cta_dispatch(const ExecArgs &a, int mode, int r0
 // Helper CTA h (of `helpers`) of a single-system SpTRSV -> SpMV launch: every (helpers *
 // blockDim)-th position of the order from its own offset (so rows come roughly in the order
 // their inputs are solved); an SpMV row's pattern and first kHelpPrefetch values are loaded,
-// then each x_j is polled in the flag buffer vb until it is set (bounded by the launch's
-// timeout).
+// then its x_j are read from the flag buffer vb, the first kHelpPrefetch together, each
+// polled again until it is set (bounded by the launch's timeout).
 constexpr int kHelpPrefetch = 6;
 template <typename T>
 __device__ __forceinline__ bool poll_value(const T *p, T &v, const ExecArgs &a, unsigned long long &t0, int row) {
@@ -253,15 +254,17 @@ __device__ void cta_helper(const ExecArgs &a, int h, int helpers, int p0, int p1
             jc[u] = ms + u < me ? __ldg(a.Mci + ms + u) : row;
             mv[u] = ms + u < me ? __ldg(Mv + ms + u) : T(0);
         }
+        // the first P operands are loaded together and only the unpublished ones polled again
+        int jw[P];
+        T xv[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) jw[u] = ms + u < me ? jc[u] : -1;
+        if (!wait_values<T, P>(vb, jw, xv, a.st, a.timeout_ns, row)) return;
         unsigned long long t0 = 0;
         T acc = T(0);
 #pragma unroll
         for (int u = 0; u < P; ++u)
-            if (ms + u < me) {
-                T xv;
-                if (!poll_value(vb + jc[u], xv, a, t0, row)) return;
-                acc += mv[u] * xv;
-            }
+            if (ms + u < me) acc += mv[u] * xv[u];
         for (int e = ms + P; e < me; ++e) {
             T xv;
             if (!poll_value(vb + __ldg(a.Mci + e), xv, a, t0, row)) return;
@@ -320,19 +323,43 @@ __global__ void __launch_bounds__(kCtaMaxThreads, 1)
 // wave, else two), each with an equal share of the SM's shared memory.
 cudaError_t launch_cta_exec(int mode, int dtype, const int *inst_ptr, const int *bperm, int cta_per_sm, int sms,
                             void *vbuf, cudaStream_t s, const ExecArgs &a, cudaEvent_t ev_start, cudaEvent_t ev_stop) {
-    int dev = 0, smax = 0, ssm = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&ssm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const int cps = cta_per_sm > 0 ? cta_per_sm : (a.n_blocks > sms ? 2 : 1);
     const int threads = kCtaMaxThreads / cps;
     const void *f = dtype == 0 ? (const void *)k_cta_exec<double> : (const void *)k_cta_exec<float>;
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, f);
-    if (e != cudaSuccess) return e;
+    // device limits and the kernel's static shared memory, looked up once per device and type
+    // (the per-call queries cost microseconds on a launch that takes tens of them)
+    struct Limits {
+        int smax, ssm;
+        long long stat;
+    };
+    static std::mutex mu;
+    static Limits lim[kMaxDevices][2];
+    static bool have[kMaxDevices][2];
+    Limits L{};
+    cudaError_t e = cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < kMaxDevices && have[dev][dtype]) {
+            L = lim[dev][dtype];
+        } else {
+            cudaDeviceGetAttribute(&L.smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaDeviceGetAttribute(&L.ssm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            cudaFuncAttributes fa{};
+            e = cudaFuncGetAttributes(&fa, f);
+            if (e != cudaSuccess) return e;
+            L.stat = (long long)fa.sharedSizeBytes;
+            if (dev < kMaxDevices) {
+                lim[dev][dtype] = L;
+                have[dev][dtype] = true;
+            }
+        }
+    }
+    const int smax = L.smax, ssm = L.ssm;
     // 1 KB of each CTA's shared memory is reserved by the system; the kernel's static shared
     // memory comes out of the same budget
-    const long long stat = (long long)fa.sharedSizeBytes;
+    const long long stat = L.stat;
     const int budget = (int)(std::min<long long>(smax - stat, (long long)ssm / cps - 1024 - stat) & ~15LL);
     if (budget < 16) return cudaErrorInvalidValue;
     // the opt-in shared-memory size is set once per device and kernel to the largest request

@@ -39,3 +39,22 @@ def test_lap2d64_counts():
     csr = lambda z: 12 * z + 4 * (n + 1)
     assert wl["fwd_bytes"] == csr(nnzL) + csr(nnzM) + 3 * 8 * n
     assert wl["fwd_flops"] == 2 * (nnzL + nnzM) + n
+
+
+def test_recorded_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    # a record counts only while the files it lists are unchanged; other sources may change
+    csrc = tmp_path / "paper_2111_12238_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cuh").write_text("kernel v1")
+    (csrc / "other.cu").write_text("launcher v1")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench._csrc_hash(["k.cuh"])
+    rec = {"w": {"fwd": {"kernel": "k", "bytes_per_launch": 1234, "sources": ["k.cuh"], "csrc_hash": h}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(__import__("json").dumps(rec))
+    assert bench._recorded_traffic("w", "fwd") == 1234
+    (csrc / "other.cu").write_text("launcher v2")
+    assert bench._recorded_traffic("w", "fwd") == 1234
+    (csrc / "k.cuh").write_text("kernel v2")
+    assert bench._recorded_traffic("w", "fwd") is None
+    assert bench._recorded_traffic("w", "adj") is None

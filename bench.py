@@ -600,8 +600,8 @@ def measure(wl, args, device, world, rank, hw):
         },
         "roofline": {
             "kernel": ("fused forward executor kernel" if dom == "fwd" else "fused adjoint executor kernel") +
-                      {2: " (row blocks)", 3: " (warp-specialised row blocks)", 4: " (packed row blocks)"}.get(
-                          mode, " (partitions)"),
+                      {2: " (row blocks)", 3: " (warp-specialised row blocks)", 4: " (packed row blocks)",
+                       5: " (single CTA per instance)"}.get(mode, " (partitions)"),
             "kernel_ms": dom_ms,
             "bound": "hbm",
             "achieved": achieved,

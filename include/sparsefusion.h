@@ -131,7 +131,9 @@ typedef struct sf_schedule sf_schedule;
  * sf_pair), its wavefront levels by parallel Kahn peeling, the linear order by
  * (level, kernel, row), and contiguous partitions of that order cut by vertex cost
  * (§3.1). Synchronises `stream` before returning. On success *out owns a new schedule;
- * on failure *out is NULL. */
+ * on failure *out is NULL. The inspector's temporary device memory comes from a stream-ordered
+ * memory pool of the library (one per device, created on first use), which keeps up to 1 GiB
+ * of freed memory for later inspections instead of returning it to the driver. */
 sf_status sf_inspect(sf_pair pair, const sf_csr *L, const sf_csr *M, const sf_options *opt,
                      void *stream, sf_schedule **out);
 

@@ -419,6 +419,7 @@ __device__ bool grid_barrier(KahnCtl *ctl, unsigned nblocks, unsigned long long 
 
 constexpr int kKahnBatch = 8;      // successors per thread whose in-degree atomics are in flight together
 constexpr int kKahnThreads = 256;
+constexpr int kKahnGroup = 8;      // lanes per frontier vertex (a warp expands four at a time)
 constexpr int kKahnLongDeg = 32 * kKahnBatch;   // longer successor lists are expanded by the whole block
 constexpr int kKahnMaxLong = 64;   // long vertices a block collects per round (more: expanded by their warp)
 
@@ -471,10 +472,10 @@ __device__ __forceinline__ void kahn_batch(int k_first, int stride, int deg1, in
 
 // Frontier peeling: round r owns the vertices whose last predecessor was removed in
 // round r-1 (its level is r); removing a vertex decrements its successors' in-degrees and
-// appends those that reach zero to the next frontier. One warp expands one frontier vertex,
-// its lanes splitting the successor list; a vertex with more than kKahnLongDeg successors is
-// set aside and expanded by all the threads of the block once the block's warps are done, so
-// one long row costs a few atomic round trips instead of one per 256 successors. Counters of
+// appends those that reach zero to the next frontier. A warp expands four frontier vertices at
+// a time, eight lanes splitting each successor list; a vertex with more than kKahnLongDeg
+// successors is set aside and expanded by all the threads of the block once the block's warps
+// are done, so one long row costs a few atomic round trips instead of one per 64 successors. Counters of
 // the next frontier are triple-buffered so that no block reads a count while another resets it.
 __global__ void __launch_bounds__(kKahnThreads) k_kahn(int n1, const int *__restrict__ s1rp, const int *__restrict__ s1ci,
                                                        const int *__restrict__ s2rp, const int *__restrict__ s2ci,
@@ -493,23 +494,40 @@ __global__ void __launch_bounds__(kKahnThreads) k_kahn(int n1, const int *__rest
     __syncthreads();
     while (fs < fe) {
         unsigned *cnt = &ctl->cnt[round % 3];
-        for (long long idx = fs + gwarp; idx < fe; idx += nwarp) {
-            const int v = queue[idx];
-            if (lane == 0) level[v] = round;
-            if (v >= n1) continue;
-            const int a1 = s1rp[v], deg1 = s1rp[v + 1] - a1;
-            const int a2 = s2rp ? s2rp[v] : 0, deg = deg1 + (s2rp ? s2rp[v + 1] - a2 : 0);
-            if (deg > kKahnLongDeg) {
-                int slot = 0;
-                if (lane == 0) slot = atomicAdd(&s_nlong, 1);
-                slot = __shfl_sync(0xffffffffu, slot, 0);
-                if (slot < kKahnMaxLong) {
-                    if (lane == 0) s_long[slot] = v;
-                    continue;
+        // a warp takes 32 / G frontier vertices at a time, G lanes each; every warp-wide
+        // operation below (the shuffles, kahn_batch) is reached by all 32 lanes
+        constexpr int G = kKahnGroup, VPW = 32 / G;
+        const int sub = lane / G, gl = lane % G;
+        for (long long base = fs + gwarp * VPW; base < fe; base += nwarp * VPW) {
+            const long long idx = base + sub;
+            int v = -1, a1 = 0, deg1 = 0, a2 = 0, deg = 0;
+            if (idx < fe) {
+                v = queue[idx];
+                if (gl == 0) level[v] = round;
+                if (v < n1) {
+                    a1 = s1rp[v];
+                    deg1 = s1rp[v + 1] - a1;
+                    deg = deg1;
+                    if (s2rp) {
+                        a2 = s2rp[v];
+                        deg += s2rp[v + 1] - a2;
+                    }
                 }
             }
-            for (int k0 = 0; k0 < deg; k0 += 32 * kKahnBatch)
-                kahn_batch(k0 + lane, 32, deg1, deg, s1ci, a1, v, s2ci, a2, n1, indeg, queue, fe, cnt);
+            // a long list goes to the whole block: the group's first lane claims a slot, and
+            // the group then expands nothing of it
+            int slot = kKahnMaxLong;
+            if (deg > kKahnLongDeg && gl == 0) {
+                slot = atomicAdd(&s_nlong, 1);
+                if (slot < kKahnMaxLong) s_long[slot] = v;
+            }
+            slot = __shfl_sync(0xffffffffu, slot, sub * G);
+            if (deg > kKahnLongDeg && slot < kKahnMaxLong) deg = deg1 = 0;
+            int maxdeg = deg;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xffffffffu, maxdeg, o));
+            for (int k0 = 0; k0 < maxdeg; k0 += G * kKahnBatch)
+                kahn_batch(k0 + gl, G, deg1, deg, s1ci, a1, v, s2ci, a2, n1, indeg, queue, fe, cnt);
         }
         __syncthreads();
         const int nl = min(s_nlong, kKahnMaxLong);

@@ -112,10 +112,13 @@ typedef struct {
                                  packed records and bulk copies (2-4: k = 1 with value flags;
                                  the call fails when a block does not fit in shared memory);
                                  5: one CTA per instance (the whole system, or each instance
-                                 of a batch) runs its joint DAG level segment by level segment
+                                 of a batch) runs its SpTRSV level segment by level segment
                                  between CTA barriers, with x (and the order and L when they
-                                 fit) in shared memory; no waits between CTAs (SF_TRSV_SPMV
-                                 forward and SF_TRSV, k = 1; block_rows is then ignored).
+                                 fit) in shared memory; the SpMV rows of a single system run
+                                 on helper CTAs of the same cooperative launch, fed x by value
+                                 (bounded waits), those of a batch on the instance's CTA after
+                                 its solve (SF_TRSV_SPMV forward and SF_TRSV, k = 1;
+                                 block_rows is then ignored).
                                  The autotuner chooses between them. */
 } sf_options;
 

@@ -66,6 +66,7 @@ def _load():
                 getattr(lib, name).restype = C.c_int
             lib.orc_partition.restype = C.c_int64
             lib.orc_block_order.restype = C.c_int64
+            lib.orc_block_order_instances.restype = C.c_int64
             lib.orc_block_segments.restype = C.c_int64
             lib.orc_reuse_ratio.restype = C.c_double
             lib.orc_reuse_ratio.argtypes = [C.c_int32, C.c_int64, C.c_int64, C.c_int64]
@@ -361,6 +362,19 @@ def block_order(kind, L, M, level, B):
     got = lib.orc_block_order(C.c_int32(kind), C.c_int32(n), lrp, lci, mrp, mci, pl, C.c_int64(int(B)), po, pbp)
     if got < 0:
         raise OracleError(got, "block_order")
+    return o, bp
+
+
+def block_order_instances(kind, n, level, inst_ptr):
+    """(order, block_ptr) with one block per instance of a block-diagonal system."""
+    lib = _load()
+    lev, pl = _i32(level)
+    ip, pip = _i32(inst_ptr)
+    o, po = _out(len(lev), np.int32)
+    bp, pbp = _out(len(ip), np.int32)
+    got = lib.orc_block_order_instances(C.c_int32(kind), C.c_int32(int(n)), pl, C.c_int32(len(ip) - 1), pip, po, pbp)
+    if got < 0:
+        raise OracleError(got, "block_order_instances")
     return o, bp
 
 

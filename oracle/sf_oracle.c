@@ -506,6 +506,42 @@ int64_t orc_block_order(int32_t kind, int32_t n, const int32_t *lrp, const int32
     return nb;
 }
 
+/* Row-block order with one block per instance of a block-diagonal system (the schedule of
+ * the single-CTA executor): instance t holds rows [inst_ptr[t], inst_ptr[t+1]); every vertex,
+ * of either kernel, belongs to the instance of its row (the instances share no entry, so no
+ * dependence crosses a block). Vertices are ordered by (block, level, tag, row). Writes
+ * order[nv] and block_ptr[n_inst+1]; returns n_inst, or -1 on a bad argument. */
+int64_t orc_block_order_instances(int32_t kind, int32_t n, const int32_t *level, int32_t n_inst,
+                                  const int32_t *inst_ptr, int32_t *order, int32_t *block_ptr) {
+    if (n_inst < 1 || inst_ptr[0] != 0 || inst_ptr[n_inst] != n) return -1;
+    const int64_t nv = (kind == 0 || kind == 3) ? 2LL * n : n;
+    int64_t *blk = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nv > 0 ? nv : 1));
+    if (!blk) return -1;
+    for (int32_t t = 0; t < n_inst; ++t) {
+        if (inst_ptr[t + 1] < inst_ptr[t]) { free(blk); return -1; }
+        for (int32_t i = inst_ptr[t]; i < inst_ptr[t + 1]; ++i) {
+            blk[i] = t;
+            if (nv > n) blk[n + i] = t;
+        }
+    }
+    int32_t depth = 0;
+    for (int64_t v = 0; v < nv; ++v)
+        if (level[v] + 1 > depth) depth = level[v] + 1;
+    const int64_t nkeys = (int64_t)n_inst * depth;
+    int64_t *start = (int64_t *)calloc((size_t)nkeys + 1, sizeof(int64_t));
+    if (!start) { free(blk); return -1; }
+    for (int64_t v = 0; v < nv; ++v) start[blk[v] * depth + level[v] + 1]++;
+    for (int64_t t = 0; t < nkeys; ++t) start[t + 1] += start[t];
+    for (int64_t b = 0; b <= n_inst; ++b) block_ptr[b] = (int32_t)start[b * depth];
+    for (int64_t v = 0; v < nv; ++v) {
+        uint32_t tag = (uint32_t)(v / n), row = (uint32_t)(v % n);
+        order[start[blk[v] * depth + level[v]]++] = (int32_t)(row | (tag << 31));
+    }
+    free(start);
+    free(blk);
+    return n_inst;
+}
+
 /* Level segments of a row-block order: a new segment starts at the first position of every
  * block and wherever the level changes from the previous position. The vertices of one
  * segment share a block and a level, so none depends on another (§2.2: every edge of the

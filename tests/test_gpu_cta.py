@@ -2,9 +2,8 @@
 runs on one CTA per instance (the whole system, or each instance of a batch) with one CTA
 barrier per level segment and x, the order and L in shared memory as far as they fit. Results
 match the FP64 oracle for both element types whatever is staged (everything, x and the order,
-x alone, nothing); exact integer systems match bit for bit; the per-instance block order is the
-(instance, level, vertex) sort of the oracle's levels; what the executor does not serve is
-refused before anything runs."""
+x alone, nothing); exact integer systems match bit for bit; the per-instance block order equals
+the oracle's; what the executor does not serve is refused before anything runs."""
 import numpy as np
 import pytest
 import torch
@@ -174,7 +173,7 @@ def test_batched_one_cta_per_instance(cps, dtype):
     assert col_rel_err(host(y3), host(y)) < TOL[dtype] and col_rel_err(host(y1), host(y)) < TOL[dtype]
 
 
-def test_per_instance_block_order_matches_definition():
+def test_per_instance_block_order_matches_oracle():
     need_cuda()
     w = I.batched_trsv_spmv(count=9, nmin=50, nmax=3000, seed=7)
     Lb = _blockdiag([x.L for x in w.instances])
@@ -184,14 +183,10 @@ def test_per_instance_block_order_matches_definition():
     got = sch.export_blocks(0)
     n = w.n
     lev = oracle.levels(oracle.SEP, Lb, Mb)
-    inst = np.repeat(np.arange(len(w.instances)), [x.n for x in w.instances])
-    v = np.arange(2 * n)
-    key_inst = np.concatenate([inst, inst])
-    perm = np.lexsort((v, lev, key_inst))
-    ref = np.where(perm < n, perm, (perm - n) | (1 << 31)).astype(np.int64).astype(np.uint32).view(np.int32)
-    assert np.array_equal(got["order"], ref)
-    sizes = np.array([2 * x.n for x in w.instances])
-    assert np.array_equal(got["block_ptr"], np.concatenate([[0], np.cumsum(sizes)]))
+    inst_ptr = np.concatenate([[0], np.cumsum([x.n for x in w.instances])]).astype(np.int32)
+    ref_o, ref_bp = oracle.block_order_instances(oracle.SEP, n, lev, inst_ptr)
+    assert np.array_equal(got["order"], ref_o)
+    assert np.array_equal(got["block_ptr"], ref_bp)
     ref_sp, ref_bs = oracle.block_segments(oracle.SEP, n, got["order"], got["block_ptr"], lev)
     assert np.array_equal(got["seg_ptr"], ref_sp) and np.array_equal(got["block_seg"], ref_bs)
     assert oracle.validate(oracle.SEP, Lb, Mb, got["order"], got["block_ptr"]) == 0

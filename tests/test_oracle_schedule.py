@@ -301,3 +301,58 @@ def test_g2_placement_keeps_every_edge_forward(kind):
     assert oracle.validate(kind, L, M, sch["order"], sch["part_ptr"]) == 0
     # paired kinds ignore the placement
     assert np.array_equal(oracle.levels(oracle.PAIRED, L, None, -1), oracle.levels(oracle.PAIRED, L, None))
+
+
+def _blockdiag(mats):
+    """Block-diagonal CSR of the given square CSRs (columns shifted by the row offsets)."""
+    n = sum(m.n_rows for m in mats)
+    rp, ci, vals, off, eoff = [np.zeros(1, np.int32)], [], [], 0, 0
+    for m in mats:
+        rp.append((np.asarray(m.rowptr[1:]) + eoff).astype(np.int32))
+        ci.append((np.asarray(m.colidx) + off).astype(np.int32))
+        vals.append(np.asarray(m.vals))
+        off += m.n_rows
+        eoff += int(m.rowptr[-1])
+    return I.Csr(n, n, np.concatenate(rp), np.concatenate(ci), np.concatenate(vals))
+
+
+@pytest.mark.parametrize("kind", [oracle.SEP, oracle.PAIRED, oracle.PAIRED_T, oracle.SEP_T])
+def test_block_order_instances_is_the_instance_level_sort(kind):
+    # one block per instance of a block-diagonal system: the (instance, level, tag, row) sort,
+    # written out here with numpy, a valid linearisation, and block pointers at the instances'
+    # vertex counts
+    sizes = [37, 1, 120, 64, 9]
+    Ls = [I.powerlaw_lower(m, 4, 20, 70 + t) for t, m in enumerate(sizes)]
+    Ms = [I.band_random(m, min(3, m), 10, 80 + t) for t, m in enumerate(sizes)]
+    L, M = _blockdiag(Ls), _blockdiag(Ms)
+    n = L.n_rows
+    useM = M if kind in (oracle.SEP, oracle.SEP_T) else None
+    lev = oracle.levels(kind, L, useM)
+    inst_ptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    o, bp = oracle.block_order_instances(kind, n, lev, inst_ptr)
+    nv = len(lev)
+    v = np.arange(nv)
+    inst = np.searchsorted(inst_ptr, v % n, side="right") - 1
+    perm = np.lexsort((v, lev, inst))
+    ref = np.where(perm < n, perm, (perm - n) | (1 << 31)).astype(np.int64).astype(np.uint32).view(np.int32)
+    assert np.array_equal(o, ref)
+    per = np.array(sizes) * (2 if nv == 2 * n else 1)
+    assert np.array_equal(bp, np.concatenate([[0], np.cumsum(per)]))
+    assert oracle.validate(kind, L, useM, o, bp) == 0
+
+
+@pytest.mark.parametrize("kind", [oracle.SEP, oracle.PAIRED, oracle.PAIRED_T, oracle.SEP_T])
+def test_block_order_instances_single_instance_is_the_one_block_order(kind):
+    w = I.spmv_trsv_powerlaw(n=300, k=1, mean=6, lmax=30, halfband=40, seed=12)
+    useM = w.M if kind in (oracle.SEP, oracle.SEP_T) else None
+    lev = oracle.levels(kind, w.L, useM)
+    o, bp = oracle.block_order_instances(kind, w.n, lev, np.array([0, w.n], np.int32))
+    ref_o, ref_bp = oracle.block_order(kind, w.L, useM, lev, 10 ** 6)
+    assert np.array_equal(o, ref_o) and np.array_equal(bp, ref_bp)
+
+
+def test_block_order_instances_rejects_bad_boundaries():
+    lev = np.zeros(10, np.int32)
+    for bad in ([0, 4], [1, 10], [0, 7, 5, 10]):
+        with pytest.raises(oracle.OracleError):
+            oracle.block_order_instances(oracle.PAIRED, 10, lev, np.array(bad, np.int32))
